@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the GFM dynamic-pressure solve on one GB300 per rank.
+
+Workload: the 2D wave tank of 1024 x 512 hex cells (524 288 cells) on
+16 m x 4 m, water depth 2 m, four wavelengths of a ka = 0.1 second-order
+Stokes surface, rho_w = 1000, rho_a = 1, g = (0, -9.81, 0), seeded random
+divergent predicted face flux; solved to a true relative residual of 1e-10.
+
+A step = one pass of the hot path on device-resident inputs: assemble the
+GFM system (interface fraction, face coefficients, jump source, cell sums),
+solve it with the mixed-precision persistent solver (FP32 inner PCG inside
+FP64 refinement), and compute the corrected face flux.  The L2 is flushed
+(a 512 MiB write) before every step.
+
+Metric: cell-iterations per second (cells x CG iterations / step time).
+Also reported: the plain FP64 GPU solve of the same system to the same
+tolerance, both solutions' error against the CPU FP64 oracle, the roofline
+of the persistent solver kernel, the CPU oracle's own rate (cpu_baseline),
+and the end-to-end rate through the host-buffer C-ABI entry point.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfm|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GFM pressure solve cell*iters/s (mixed FP32-inner + FP64 refinement, rtol 1e-10)"
+UNIT = "cell*iters/s"
+WORKLOAD = "tank2d_1024x512: 2D wave tank 1024x512x1 hexes on 16 m x 4 m, ka=0.1, 4 wavelengths, depth 2 m"
+RTOL = 1e-10
+INNER_RTOL = 1e-4
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gfm", "reference"], default="gfm")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the solver kernel from a committed ncu summary,
+    valid only while the kernel source is unchanged (else None)."""
+    src = os.path.join(ROOT, "paper_1804_01130_gb300", "csrc", "gfm_solve.cu")
+    with open(src, "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        r = rec.get("k_solve_mixed", {})
+        if r.get("source_sha") == sha:
+            return r, sha
+    except Exception:
+        pass
+    return None, sha
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def _case():
+    import cases
+    return cases.make_case(2)
+
+
+def _cpu_baseline(case, seconds: float):
+    """The CPU oracle (as it stands) timed on the host cores: fixed-count
+    Jacobi-PCG iterations on the assembled system, sized to ~`seconds`."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    fc = oracle.faces(case)
+    sy = oracle.assemble(case, fc)
+    t = time.perf_counter()
+    oracle.pcg_fixed(sy, 10)
+    per = max((time.perf_counter() - t) / 10, 1e-6)
+    iters = max(10, int(seconds / per))
+    t = time.perf_counter()
+    oracle.pcg_fixed(sy, iters)
+    dt = time.perf_counter() - t
+    return {"value": case.n * iters / dt, "unit": UNIT, "cores": int(oracle.max_threads()), "kind": "oracle",
+            "sample": f"{iters} Jacobi-PCG iterations of the FP64 CSR oracle on the full {case.n}-cell tank "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU FP64 oracle, as it stands, on the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    case = _case()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    fc = oracle.faces(case)
+    sy = oracle.assemble(case, fc)
+    t = time.perf_counter()
+    oracle.pcg_fixed(sy, 10)
+    per = max((time.perf_counter() - t) / 10, 1e-6)
+    iters = max(10, int(2.0 / per))  # ~2 s per step
+    for _ in range(args.warmup):
+        oracle.pcg_fixed(sy, iters)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pcg_fixed(sy, iters)
+    dt = time.perf_counter() - t
+    value = case.n * iters * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": case.n, "faces": case.F, "rtol": RTOL,
+                   "sample": f"{iters} PCG iterations per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(oracle.max_threads()), "kind": "oracle",
+                         "sample": f"{iters} Jacobi-PCG iterations per step of the FP64 CSR oracle, full tank"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gfm(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    import paper_1804_01130_gb300 as g
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = _case()
+    n, F = case.n, case.F
+    stream = torch.cuda.current_stream()
+
+    p_oracle = None
+    if rank == 0 and not args.no_oracle_check:
+        import oracle
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        oracle.set_threads(cores)
+        fc = oracle.faces(case)
+        sy = oracle.assemble(case, fc)
+        p_oracle, _, _, _ = oracle.pcg(sy, rtol=1e-12)
+
+    s = g.GFM.from_case(case, renumber=1)
+    alpha = torch.as_tensor(case.alpha).to(dev)
+    phi = torch.as_tensor(case.phi).to(dev)
+    p = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    phys = dict(rho_w=case.rho_w, rho_a=case.rho_a, g=case.g, ref_cell=case.ref_cell, ref_value=case.ref_value)
+
+    def step(i, ev=None):
+        flush.fill_(float(i))
+        s.assemble(alpha, phi, **phys)
+        if ev is not None:
+            ev[0].record(stream)
+        out = s.solve(mode="mixed", rtol=RTOL, inner_rtol=INNER_RTOL, phi_corr=True, info_on_device=True, out=p)
+        if ev is not None:
+            ev[1].record(stream)
+        return out
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    info = g.GFM.info_from_device(s._info_dev)
+    if info.status != 0:
+        raise SystemExit(f"mixed solve failed: {info}")
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    lt0 = s.profile().launches_total
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    clk.start()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(1000 + i, evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    launches = s.profile().launches_total - lt0
+    info = g.GFM.info_from_device(s._info_dev)
+    kernel_ms = [a.elapsed_time(b) for a, b in evs]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    iters = info.iters
+    value = world * n * iters / (ms_step * 1e-3)
+
+    # accuracy of the mixed solution, then the plain FP64 solve of the same system
+    p_mixed = p.detach().cpu().numpy()
+    s.assemble(alpha, phi, **phys)
+    fp64_ms = []
+    for i in range(2):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p64, _, info64 = s.solve(mode="fp64", rtol=RTOL, phi_corr=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms.append(a.elapsed_time(b))
+    p_fp64 = p64.detach().cpu().numpy()
+    acc = {}
+    if p_oracle is not None:
+        nrm = float(np.linalg.norm(p_oracle))
+        acc = {"mixed_rel_l2_vs_oracle": float(np.linalg.norm(p_mixed - p_oracle) / nrm),
+               "fp64_rel_l2_vs_oracle": float(np.linalg.norm(p_fp64 - p_oracle) / nrm)}
+
+    # roofline of the persistent solver kernel (the window also holds three
+    # small memsets and the corrected-flux kernel, < 0.1% of it)
+    kms = statistics.mean(kernel_ms)
+    alg_bytes = n * iters * (52 + 12 * F / n) + n * info.refinements * (24 + 16 * F / n)
+    achieved = alg_bytes / (kms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    trec, sha = _traffic_record()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (trec["dram_bytes_per_launch"] if trec else None),
+            "kernel": "k_solve_mixed", "kernel_ms": kms, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "bytes_model": "(52 + 12 F/n) B per cell-iteration + (24 + 16 F/n) B per cell per refinement",
+            "note": "config-2 working set (~35 MB) is L2-resident across iterations"}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if rank == 0:
+        a_h = torch.as_tensor(case.alpha).contiguous().pin_memory()
+        f_h = torch.as_tensor(case.phi).contiguous().pin_memory()
+        p_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+        s.solve_host(a_h, f_h, p_h, mode="mixed", rtol=RTOL, inner_rtol=INNER_RTOL, **phys)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = 0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            inf = s.solve_host(a_h, f_h, p_h, mode="mixed", rtol=RTOL, inner_rtol=INNER_RTOL, **phys)
+            its += inf.iters
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * n * its / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (n + F),
+               "d2h_bytes_per_step": 8 * n + 32, "ms_per_step": dt / args.steps * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(case, args.cpu_seconds)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": n, "faces": F, "rtol": RTOL, "inner_rtol": INNER_RTOL,
+                   "mode": "mixed", "renumber": "rcm", "parallelism": f"replicas{world}",
+                   "l2": "flushed (512 MiB write) before every step", "inputs": "device-resident"},
+        "iters_per_solve": iters, "refinements": info.refinements, "rel_res_l2": info.rel_res_l2,
+        "fp64": {"ms_per_solve": statistics.mean(fp64_ms), "iters": info64.iters,
+                 "cell_iters_per_s": n * info64.iters / (statistics.mean(fp64_ms) * 1e-3),
+                 "rel_res_l2": info64.rel_res_l2},
+        "mixed_solve_ms": kms,
+        "speedup_mixed_vs_fp64_time_to_tol": statistics.mean(fp64_ms) / kms,
+        "accuracy": acc,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    rank, local, world = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gfm(args, rank, local, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * gfm.h -- C ABI of libgfm: the Ghost Fluid Method dynamic-pressure equation
+ * (assembly + iterative solve + adjoint) on one GB300 GPU.
+ *
+ * The method is that of Sec. 3.1 of Vukcevic, Roenby, Gatin & Jasak, "A sharp
+ * free surface finite volume method applied to gravity wave flows": the
+ * continuity equation (Eq. 1) turned into a pressure equation for the dynamic
+ * pressure p_d = p - rho g.x (Eq. 3), discretised on a face-addressed
+ * finite-volume mesh (Sec. 3, owner P / neighbour N, area vector S_f, centre
+ * distance d_f) with the ghost-fluid interface treatment of Eqs. 12-20 and the
+ * jump conditions Eqs. 7-8.
+ *
+ * General rules for every call:
+ *  - Array arguments are DEVICE pointers (memory of the current CUDA device,
+ *    e.g. allocated by PyTorch) unless the comment says host.  They stay owned
+ *    by the caller.  The library owns only the opaque handle and its workspace.
+ *  - Arrays are structure-of-arrays FP64 unless noted: a 3-vector field over
+ *    m items is laid out [3][m] (all x, then all y, then all z).
+ *  - Cell arrays are indexed by the caller's cell numbering, face arrays by
+ *    the caller's internal-face numbering.  Any internal renumbering is
+ *    invisible to the caller.
+ *  - Work is stream-ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  A call returns once the work is enqueued, except where noted.
+ *  - Every call returns a gfm_status; no C++ exception or process exit ever
+ *    crosses this boundary.  gfm_last_error(h) describes the last failure.
+ *  - Inputs are never modified.  Outputs may not alias inputs unless noted.
+ *  - A handle is not thread-safe: one host thread and one stream at a time.
+ */
+#ifndef GFM_H
+#define GFM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GFM_OK = 0,
+    GFM_ERR_ARG = 1,           /* invalid argument (host-checked)                          */
+    GFM_ERR_CUDA = 2,          /* a CUDA runtime call failed                               */
+    GFM_ERR_NOMEM = 3,         /* device or host allocation failed                         */
+    GFM_ERR_NOT_CONVERGED = 4, /* max_iters / max_refine reached; p holds the last iterate */
+    GFM_ERR_BREAKDOWN = 5,     /* CG breakdown (p^T A p <= 0 or not finite)                */
+    GFM_ERR_TIMEOUT = 6,       /* a grid-barrier wait exceeded its time budget             */
+    GFM_ERR_INCOMPATIBLE = 7,  /* unpinned system with an incompatible right-hand side     */
+    GFM_ERR_STATE = 8          /* call out of order (e.g. solve before assemble)           */
+} gfm_status;
+
+typedef struct gfm_ctx *gfm_handle;
+typedef void *gfm_stream; /* cudaStream_t */
+
+/*
+ * Face-addressed mesh (Sec. 3, Fig. "polyhedral control volume").
+ *  n_cells, n_faces : number of cells and of INTERNAL faces (> 0).  Boundary
+ *                     faces are walls: zero flux, zero-gradient p_d, and are
+ *                     not listed.
+ *  owner, neighbour : int32 [n_faces], 0 <= owner[f] < neighbour[f] < n_cells.
+ *  Sf               : [3][n_faces] face area vectors pointing owner -> neighbour.
+ *  C                : [3][n_cells] cell centres (absolute coordinates: the
+ *                     jump source uses g.x_Gamma with x absolute, Eq. 7).
+ *  V                : [n_cells] cell volumes, or NULL (not used by the solve).
+ * The arrays are read during gfm_create only (the handle keeps its own copy).
+ */
+typedef struct {
+    int32_t n_cells;
+    int32_t n_faces;
+    const int32_t *owner;
+    const int32_t *neighbour;
+    const double *Sf;
+    const double *C;
+    const double *V;
+} gfm_mesh;
+
+/*
+ * Physics of one problem (host struct).
+ *  rho_w, rho_a : heavy (water, "+") and light (air, "-") densities, Eq. 4;
+ *                 0 < rho_a <= rho_w.
+ *  g            : gravitational acceleration vector (Eq. 3).
+ *  ref_cell     : cell whose p_d is pinned to ref_value (caller numbering),
+ *                 or -1 for no pin (then the right-hand side must be
+ *                 compatible, sum(b) ~ 0, else GFM_ERR_INCOMPATIBLE at solve).
+ *                 The pin doubles that cell's diagonal and adds
+ *                 diag * ref_value to its source, so A stays symmetric
+ *                 positive definite; a compatible system's solution does not
+ *                 depend on the pin's size.
+ */
+typedef struct {
+    double rho_w;
+    double rho_a;
+    double g[3];
+    int32_t ref_cell;
+    double ref_value;
+} gfm_phys;
+
+typedef enum {
+    GFM_FP64 = 0,  /* Jacobi-PCG entirely in FP64                                       */
+    GFM_MIXED = 1  /* FP32 inner Jacobi-PCG (FP64-accurate dot sums) inside FP64
+                      iterative refinement: true residual, correction and the jump
+                      source stay FP64                                                  */
+} gfm_mode;
+
+/*
+ * Solver options (host struct; gfm_default_opts fills sensible values).
+ *  rtol       : stop when ||b - A p||_2 <= rtol ||b||_2, the TRUE FP64 residual.
+ *  inner_rtol : MIXED only: relative residual reduction of each FP32 inner solve.
+ *  max_iters  : cap on CG iterations (inner iterations summed, MIXED).
+ *  max_refine : MIXED: cap on refinement steps; FP64: cap on restarts from the
+ *               true residual.
+ *  use_x0     : 1 = start from the p passed in, 0 = start from zero.
+ *  info_on_device : 1 = `info` is a DEVICE pointer written by the solve, and
+ *               the call returns without synchronising (graph-capturable);
+ *               0 = `info` is a host pointer (or NULL) and the call
+ *               synchronises `stream` to fill it and to return the status.
+ *  timeout_ms : budget of ONE grid-barrier wait inside the persistent kernel;
+ *               on expiry the kernel records GFM_ERR_TIMEOUT and all CTAs
+ *               return (the device stays usable).
+ */
+typedef struct {
+    int32_t mode;
+    double rtol;
+    double inner_rtol;
+    int32_t max_iters;
+    int32_t max_refine;
+    int32_t use_x0;
+    int32_t info_on_device;
+    double timeout_ms;
+} gfm_solve_opts;
+
+/* Result of a solve.  iters = CG iterations (summed over refinements),
+ * refinements = outer steps (MIXED) or true-residual checks (FP64),
+ * status = a gfm_status, rel_res_l2 = final ||b - A p||_2 / ||b||_2 (FP64),
+ * rel_res_l1 = OpenFOAM-style normalised L1 residual of the same p. */
+typedef struct {
+    int32_t iters;
+    int32_t refinements;
+    int32_t status;
+    int32_t reserved;
+    double rel_res_l2;
+    double rel_res_l1;
+} gfm_solve_info;
+
+/* Launch shape of the persistent solver kernels (autotuned or set). */
+typedef struct {
+    int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)       */
+    int32_t ctas_per_sm; /* co-resident CTAs per SM (grid = SMs x this)     */
+} gfm_tuning;
+
+/* Timings of the last call, recorded with CUDA events on the launching
+ * stream when profiling is on (gfm_set_profiling); launch counts always. */
+typedef struct {
+    float ms_assemble;   /* face + cell assembly kernels             */
+    float ms_solve;      /* the persistent solver kernel alone       */
+    float ms_total;      /* everything enqueued by the last call     */
+    int32_t launches;    /* kernels launched by the last call        */
+    int32_t grid;        /* CTAs of the persistent kernel            */
+    int32_t threads;     /* threads per CTA of the persistent kernel */
+    int32_t launches_total; /* kernels launched since gfm_create         */
+} gfm_profile;
+
+/* Fill `opts` with defaults: FP64, rtol 1e-10, inner_rtol 1e-4, max_iters 1e6,
+ * max_refine 30, use_x0 0, info_on_device 0, timeout_ms 2000. */
+gfm_status gfm_default_opts(gfm_solve_opts *opts);
+
+/*
+ * Build a handle for one mesh.  Validates indices on the host (the index
+ * arrays are copied to the host once), renumbers cells for locality
+ * (renumber: 0 = keep the caller's order, 1 = reverse Cuthill-McKee,
+ * 2 = Morton order of the cell centres) and builds the sliced-ELL
+ * cell-to-face tables.  Synchronises `stream`.  Errors: GFM_ERR_ARG (bad
+ * sizes, owner >= neighbour, index out of range, NULL arrays),
+ * GFM_ERR_NOMEM, GFM_ERR_CUDA.
+ */
+gfm_status gfm_create(const gfm_mesh *mesh, int32_t renumber, gfm_stream stream, gfm_handle *out);
+
+/* Release the handle and its device workspace (synchronises the device). */
+gfm_status gfm_destroy(gfm_handle h);
+
+/*
+ * Assemble the GFM pressure equation A p = b (Sec. 3.1) for volume fraction
+ * alpha [n] (Eq. 10) and predicted face flux phi [F] (the Rhie-Chow flux of
+ * the momentum predictor, oriented owner -> neighbour):
+ *   wet cell: alpha >= 0.5; interface face: wet owner != wet neighbour;
+ *   lambda_W = (alpha_W - 0.5)/(alpha_W - alpha_D) from the wet cell (Eq. 13);
+ *   gamma_f = c_f / (lambda_W rho_w + (1 - lambda_W) rho_a), c_f = S.S/S.d
+ *     (Eqs. 16-18, 20 collapsed; lambda := 1 or 0 off the interface);
+ *   H_f = (rho_w - rho_a) g.(x_W + lambda_W (x_D - x_W))   (Eqs. 7, 12);
+ *   J_f = +H_f if the owner is wet, -H_f if dry, 0 elsewhere;
+ *   A_ii = sum gamma_f, A_{o,nb} = -gamma_f; b_i = -sum s_if (phi_f + gamma_f J_f).
+ * Face quantities and the per-cell sums (ascending face order) are computed
+ * in FP64 with every operation rounded as written (bit-reproducible).
+ * Errors: GFM_ERR_ARG (NULL, rho_a <= 0, rho_w < rho_a, ref_cell out of range).
+ */
+gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, const gfm_phys *phys,
+                        gfm_stream stream);
+
+/*
+ * Copy the assembled system out (for tests and diagnostics).  Any pointer may
+ * be NULL.  lambda, gamma, jump: [F] face order; diag, b: [n] cell order, with
+ * the pin applied.  Errors: GFM_ERR_STATE before gfm_assemble.
+ */
+gfm_status gfm_export_system(gfm_handle h, double *lambda, double *gamma, double *jump, double *diag, double *b,
+                             gfm_stream stream);
+
+/*
+ * Solve A p = b.  p [n]: in = x0 when opts->use_x0, out = p_d.  phi_corr [F]
+ * (nullable): corrected face flux phi_f - gamma_f (p_nb - p_own - J_f), zero in
+ * still water (balanced force, Sec. 3.1).  info: see info_on_device.
+ * Returns GFM_OK, GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN, GFM_ERR_TIMEOUT,
+ * GFM_ERR_INCOMPATIBLE (when synchronising), GFM_ERR_STATE before assemble,
+ * GFM_ERR_ARG.  With info_on_device = 1 the solve status is only in info.
+ */
+gfm_status gfm_solve(gfm_handle h, const gfm_solve_opts *opts, double *p, double *phi_corr, gfm_solve_info *info,
+                     gfm_stream stream);
+
+/*
+ * Reverse mode of p = A(alpha)^{-1} b(alpha, phi): given p (the solution of
+ * the last assembled system) and dL/dp [n], solve the adjoint system A mu =
+ * dL/dp (A is symmetric) and return
+ *   dL_dphi [F]   = -(mu_own - mu_nb),
+ *   dL_dalpha [n] = sum over interface faces of dL/dlambda_f * dlambda_f/dalpha,
+ * through gamma_f(lambda_f) and J_f(lambda_f) (Eqs. 13, 18, 7, 12); wet/dry
+ * flags and the pin's size are held fixed.  mu [n] nullable.  Same options
+ * and errors as gfm_solve.
+ */
+gfm_status gfm_solve_adjoint(gfm_handle h, const gfm_solve_opts *opts, const double *p, const double *dL_dp,
+                             double *dL_dphi, double *dL_dalpha, double *mu, gfm_solve_info *info, gfm_stream stream);
+
+/*
+ * End-to-end call on HOST buffers: copies alpha [n] and phi [F] to the
+ * device, assembles, solves and copies p [n] back, all on `stream`, and
+ * synchronises.  Host buffers should be page-locked for the copies to run
+ * asynchronously.  p_host is x0 when opts->use_x0.  info is a host pointer.
+ */
+gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *phi_host, const gfm_phys *phys,
+                          const gfm_solve_opts *opts, double *p_host, gfm_solve_info *info, gfm_stream stream);
+
+/* Launch shape of the persistent kernels.  threads = 0 / ctas_per_sm = 0 keep
+ * the current value.  Errors: GFM_ERR_ARG if the shape cannot be co-resident. */
+gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t);
+gfm_status gfm_get_tuning(gfm_handle h, gfm_tuning *t);
+
+/* Profiling: on = 1 records CUDA events around every kernel of each call. */
+gfm_status gfm_set_profiling(gfm_handle h, int32_t on);
+gfm_status gfm_get_profile(gfm_handle h, gfm_profile *out);
+
+/* Sizes: cells, internal faces, tanks, and the internal cell order
+ * (perm[i] = internal index of caller cell i), perm may be NULL (host). */
+gfm_status gfm_get_sizes(gfm_handle h, int32_t *n_cells, int32_t *n_faces, int32_t *n_tanks);
+gfm_status gfm_get_permutation(gfm_handle h, int32_t *perm_host);
+
+const char *gfm_status_string(gfm_status s);
+const char *gfm_last_error(gfm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFM_H */

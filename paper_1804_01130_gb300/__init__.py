@@ -1,0 +1,361 @@
+"""GB300-native Ghost Fluid Method pressure solver (arXiv 1804.01130, Sec. 3.1).
+
+A thin ctypes binding over libgfm (C ABI in include/gfm.h).  Every step of the
+path -- assembly, solve, corrected flux, adjoint -- runs in libgfm's CUDA
+kernels; this module only marshals arguments.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: without a built libgfm and a
+CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "GFMError", "SolveInfo", "Profile", "GFM", "GFMSolve", "load_library", "library_path",
+    "GFM_OK", "GFM_ERR_ARG", "GFM_ERR_CUDA", "GFM_ERR_NOMEM", "GFM_ERR_NOT_CONVERGED", "GFM_ERR_BREAKDOWN",
+    "GFM_ERR_TIMEOUT", "GFM_ERR_INCOMPATIBLE", "GFM_ERR_STATE", "EXPORTED_SYMBOLS",
+]
+
+(GFM_OK, GFM_ERR_ARG, GFM_ERR_CUDA, GFM_ERR_NOMEM, GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN, GFM_ERR_TIMEOUT,
+ GFM_ERR_INCOMPATIBLE, GFM_ERR_STATE) = range(9)
+GFM_FP64, GFM_MIXED = 0, 1
+MODES = {"fp64": GFM_FP64, "mixed": GFM_MIXED}
+
+EXPORTED_SYMBOLS = (
+    "gfm_default_opts", "gfm_create", "gfm_destroy", "gfm_assemble", "gfm_export_system", "gfm_solve",
+    "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
+    "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
+)
+
+
+class GFMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class _Mesh(ct.Structure):
+    _fields_ = [("n_cells", ct.c_int32), ("n_faces", ct.c_int32), ("owner", ct.c_void_p),
+                ("neighbour", ct.c_void_p), ("Sf", ct.c_void_p), ("C", ct.c_void_p), ("V", ct.c_void_p)]
+
+
+class _Phys(ct.Structure):
+    _fields_ = [("rho_w", ct.c_double), ("rho_a", ct.c_double), ("g", ct.c_double * 3), ("ref_cell", ct.c_int32),
+                ("ref_value", ct.c_double)]
+
+
+class _Opts(ct.Structure):
+    _fields_ = [("mode", ct.c_int32), ("rtol", ct.c_double), ("inner_rtol", ct.c_double),
+                ("max_iters", ct.c_int32), ("max_refine", ct.c_int32), ("use_x0", ct.c_int32),
+                ("info_on_device", ct.c_int32), ("timeout_ms", ct.c_double)]
+
+
+class _Info(ct.Structure):
+    _fields_ = [("iters", ct.c_int32), ("refinements", ct.c_int32), ("status", ct.c_int32),
+                ("reserved", ct.c_int32), ("rel_res_l2", ct.c_double), ("rel_res_l1", ct.c_double)]
+
+
+class _Tuning(ct.Structure):
+    _fields_ = [("threads", ct.c_int32), ("ctas_per_sm", ct.c_int32)]
+
+
+class _Profile(ct.Structure):
+    _fields_ = [("ms_assemble", ct.c_float), ("ms_solve", ct.c_float), ("ms_total", ct.c_float),
+                ("launches", ct.c_int32), ("grid", ct.c_int32), ("threads", ct.c_int32),
+                ("launches_total", ct.c_int32)]
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    refinements: int
+    status: int
+    rel_res_l2: float
+    rel_res_l1: float
+
+
+@dataclass
+class Profile:
+    ms_assemble: float
+    ms_solve: float
+    ms_total: float
+    launches: int
+    grid: int
+    threads: int
+    launches_total: int
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libgfm (building it first if needed).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise GFMError(GFM_ERR_CUDA, f"libgfm not built: {path}")
+    lib = ct.CDLL(path)
+    P, I, S = ct.c_void_p, ct.c_int32, ct.c_int
+    sig = {
+        "gfm_default_opts": ([ct.POINTER(_Opts)], S),
+        "gfm_create": ([ct.POINTER(_Mesh), I, P, ct.POINTER(P)], S),
+        "gfm_destroy": ([P], S),
+        "gfm_assemble": ([P, P, P, ct.POINTER(_Phys), P], S),
+        "gfm_export_system": ([P, P, P, P, P, P, P], S),
+        "gfm_solve": ([P, ct.POINTER(_Opts), P, P, P, P], S),
+        "gfm_solve_adjoint": ([P, ct.POINTER(_Opts), P, P, P, P, P, P, P], S),
+        "gfm_solve_host": ([P, P, P, ct.POINTER(_Phys), ct.POINTER(_Opts), P, P, P], S),
+        "gfm_set_tuning": ([P, ct.POINTER(_Tuning)], S),
+        "gfm_get_tuning": ([P, ct.POINTER(_Tuning)], S),
+        "gfm_set_profiling": ([P, I], S),
+        "gfm_get_profile": ([P, ct.POINTER(_Profile)], S),
+        "gfm_get_sizes": ([P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)], S),
+        "gfm_get_permutation": ([P, P], S),
+        "gfm_status_string": ([S], ct.c_char_p),
+        "gfm_last_error": ([P], ct.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise GFMError(GFM_ERR_ARG, "libgfm takes CUDA tensors (device memory)")
+    if not t.is_contiguous():
+        raise GFMError(GFM_ERR_ARG, "libgfm takes contiguous tensors")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _f64(x, device) -> torch.Tensor:
+    t = torch.as_tensor(x)
+    return t.to(device=device, dtype=torch.float64).contiguous()
+
+
+def _i32(x, device) -> torch.Tensor:
+    return torch.as_tensor(x).to(device=device, dtype=torch.int32).contiguous()
+
+
+class GFM:
+    """One mesh's GFM pressure system on the current CUDA device.
+
+    Parameters mirror gfm_create: owner/neighbour [F] int32, Sf [3, F], C [3, n]
+    (any array-likes; copied to the device), renumber 0/1/2 (none/RCM/Morton).
+    """
+
+    def __init__(self, owner, neighbour, Sf, C, V=None, renumber: int = 1, device=None, stream=None):
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise GFMError(GFM_ERR_CUDA, "no CUDA device: libgfm has no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        d = self.device
+        self.owner = _i32(owner, d)
+        self.neighbour = _i32(neighbour, d)
+        self.Sf = _f64(Sf, d).reshape(3, -1).contiguous()
+        self.C = _f64(C, d).reshape(3, -1).contiguous()
+        self.n = int(self.C.shape[1])
+        self.F = int(self.owner.numel())
+        mesh = _Mesh(self.n, self.F, self.owner.data_ptr(), self.neighbour.data_ptr(), self.Sf.data_ptr(),
+                     self.C.data_ptr(), None)
+        h = ct.c_void_p()
+        with torch.cuda.device(d):
+            st = self.lib.gfm_create(ct.byref(mesh), int(renumber), _stream(stream), ct.byref(h))
+        if st != GFM_OK:
+            raise GFMError(st, f"gfm_create: {self.lib.gfm_status_string(st).decode()}")
+        self.h = h
+        self.phys = None
+        self._info_dev = torch.zeros(4, dtype=torch.float64, device=d)  # 32 bytes = gfm_solve_info
+
+    @classmethod
+    def from_case(cls, case, renumber: int = 1, **kw) -> "GFM":
+        return cls(case.owner, case.neighbour, case.Sf, case.C, renumber=renumber, **kw)
+
+    # -- helpers ----------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != GFM_OK:
+            msg = self.lib.gfm_last_error(self.h).decode()
+            raise GFMError(st, f"{what}: {self.lib.gfm_status_string(st).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gfm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def make_phys(rho_w=1000.0, rho_a=1.0, g=(0.0, -9.81, 0.0), ref_cell=0, ref_value=0.0) -> _Phys:
+        return _Phys(float(rho_w), float(rho_a), (ct.c_double * 3)(*[float(v) for v in g]), int(ref_cell),
+                     float(ref_value))
+
+    def make_opts(self, mode="mixed", rtol=1e-10, inner_rtol=1e-4, max_iters=1_000_000, max_refine=30,
+                  use_x0=False, info_on_device=False, timeout_ms=2000.0) -> _Opts:
+        o = _Opts()
+        self.lib.gfm_default_opts(ct.byref(o))
+        o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        o.rtol = float(rtol)
+        o.inner_rtol = float(inner_rtol)
+        o.max_iters = int(max_iters)
+        o.max_refine = int(max_refine)
+        o.use_x0 = int(bool(use_x0))
+        o.info_on_device = int(bool(info_on_device))
+        o.timeout_ms = float(timeout_ms)
+        return o
+
+    # -- ABI calls ----------------------------------------------------------
+    def assemble(self, alpha: torch.Tensor, phi: torch.Tensor, rho_w=1000.0, rho_a=1.0, g=(0.0, -9.81, 0.0),
+                 ref_cell=0, ref_value=0.0, stream=None):
+        alpha = _f64(alpha, self.device)
+        phi = _f64(phi, self.device)
+        self.phys = self.make_phys(rho_w, rho_a, g, ref_cell, ref_value)
+        self._check(self.lib.gfm_assemble(self.h, _ptr(alpha), _ptr(phi), ct.byref(self.phys), _stream(stream)),
+                    "gfm_assemble")
+
+    def export_system(self, stream=None) -> dict:
+        d = self.device
+        out = {k: torch.empty(self.F, dtype=torch.float64, device=d) for k in ("lambda", "gamma", "jump")}
+        out.update({k: torch.empty(self.n, dtype=torch.float64, device=d) for k in ("diag", "b")})
+        self._check(self.lib.gfm_export_system(self.h, _ptr(out["lambda"]), _ptr(out["gamma"]), _ptr(out["jump"]),
+                                               _ptr(out["diag"]), _ptr(out["b"]), _stream(stream)),
+                    "gfm_export_system")
+        return out
+
+    def solve(self, mode="mixed", rtol=1e-10, inner_rtol=1e-4, p0=None, phi_corr=False, max_iters=1_000_000,
+              max_refine=30, info_on_device=False, timeout_ms=2000.0, out=None, raise_on_error=True, stream=None):
+        """Solve the assembled system; returns (p, phi_corr or None, SolveInfo or device tensor)."""
+        p = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
+        if p0 is not None:
+            p.copy_(_f64(p0, self.device))
+        fc = torch.empty(self.F, dtype=torch.float64, device=self.device) if phi_corr else None
+        o = self.make_opts(mode, rtol, inner_rtol, max_iters, max_refine, p0 is not None, info_on_device, timeout_ms)
+        if info_on_device:
+            st = self.lib.gfm_solve(self.h, ct.byref(o), _ptr(p), _ptr(fc), _ptr(self._info_dev), _stream(stream))
+            self._check(st, "gfm_solve")
+            return p, fc, self._info_dev
+        info = _Info()
+        st = self.lib.gfm_solve(self.h, ct.byref(o), _ptr(p), _ptr(fc), ct.byref(info), _stream(stream))
+        si = SolveInfo(info.iters, info.refinements, info.status, info.rel_res_l2, info.rel_res_l1)
+        if st != GFM_OK and (raise_on_error or st not in (GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN,
+                                                          GFM_ERR_TIMEOUT)):
+            self._check(st, "gfm_solve")
+        return p, fc, si
+
+    def adjoint(self, p: torch.Tensor, dL_dp: torch.Tensor, mode="fp64", rtol=1e-12, inner_rtol=1e-4,
+                max_iters=1_000_000, timeout_ms=2000.0, stream=None):
+        """Returns (dL/dphi [F], dL/dalpha [n], mu [n], SolveInfo)."""
+        d = self.device
+        p = _f64(p, d)
+        g = _f64(dL_dp, d)
+        dphi = torch.empty(self.F, dtype=torch.float64, device=d)
+        dalpha = torch.empty(self.n, dtype=torch.float64, device=d)
+        mu = torch.empty(self.n, dtype=torch.float64, device=d)
+        o = self.make_opts(mode, rtol, inner_rtol, max_iters, 30, False, False, timeout_ms)
+        info = _Info()
+        st = self.lib.gfm_solve_adjoint(self.h, ct.byref(o), _ptr(p), _ptr(g), _ptr(dphi), _ptr(dalpha), _ptr(mu),
+                                        ct.byref(info), _stream(stream))
+        self._check(st, "gfm_solve_adjoint")
+        return dphi, dalpha, mu, SolveInfo(info.iters, info.refinements, info.status, info.rel_res_l2,
+                                           info.rel_res_l1)
+
+    def solve_host(self, alpha_host: torch.Tensor, phi_host: torch.Tensor, p_host: torch.Tensor, mode="mixed",
+                   rtol=1e-10, inner_rtol=1e-4, rho_w=1000.0, rho_a=1.0, g=(0.0, -9.81, 0.0), ref_cell=0,
+                   ref_value=0.0, stream=None) -> SolveInfo:
+        """End-to-end call on host (ideally pinned) float64 tensors; p_host is filled."""
+        for t in (alpha_host, phi_host, p_host):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise GFMError(GFM_ERR_ARG, "solve_host takes contiguous float64 host tensors")
+        self.phys = self.make_phys(rho_w, rho_a, g, ref_cell, ref_value)
+        o = self.make_opts(mode, rtol, inner_rtol)
+        info = _Info()
+        st = self.lib.gfm_solve_host(self.h, ct.c_void_p(alpha_host.data_ptr()), ct.c_void_p(phi_host.data_ptr()),
+                                     ct.byref(self.phys), ct.byref(o), ct.c_void_p(p_host.data_ptr()),
+                                     ct.byref(info), _stream(stream))
+        self._check(st, "gfm_solve_host")
+        return SolveInfo(info.iters, info.refinements, info.status, info.rel_res_l2, info.rel_res_l1)
+
+    def set_tuning(self, threads=0, ctas_per_sm=0):
+        self._check(self.lib.gfm_set_tuning(self.h, ct.byref(_Tuning(int(threads), int(ctas_per_sm)))),
+                    "gfm_set_tuning")
+
+    def get_tuning(self):
+        t = _Tuning()
+        self._check(self.lib.gfm_get_tuning(self.h, ct.byref(t)), "gfm_get_tuning")
+        return t.threads, t.ctas_per_sm
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.gfm_set_profiling(self.h, int(bool(on))), "gfm_set_profiling")
+
+    def profile(self) -> Profile:
+        pr = _Profile()
+        self._check(self.lib.gfm_get_profile(self.h, ct.byref(pr)), "gfm_get_profile")
+        return Profile(pr.ms_assemble, pr.ms_solve, pr.ms_total, pr.launches, pr.grid, pr.threads,
+                       pr.launches_total)
+
+    def permutation(self):
+        import numpy as np
+        perm = np.empty(self.n, dtype=np.int32)
+        self._check(self.lib.gfm_get_permutation(self.h, ct.c_void_p(perm.ctypes.data)), "gfm_get_permutation")
+        return perm
+
+    @staticmethod
+    def info_from_device(t: torch.Tensor) -> SolveInfo:
+        raw = t.detach().cpu().numpy().tobytes()
+        info = _Info.from_buffer_copy(raw)
+        return SolveInfo(info.iters, info.refinements, info.status, info.rel_res_l2, info.rel_res_l1)
+
+
+class GFMSolve(torch.autograd.Function):
+    """p = GFMSolve.apply(alpha, phi, gfm, phys_kwargs, solve_kwargs): differentiable GFM pressure solve.
+
+    Forward assembles and solves; backward solves the adjoint system (A is
+    symmetric) in libgfm and returns dL/dalpha and dL/dphi.  Only (alpha, phi,
+    p) are saved: no Krylov state is stored; the system is re-assembled in
+    backward if the handle was re-assembled since.
+    """
+
+    @staticmethod
+    def forward(ctx, alpha, phi, gfm: GFM, phys_kwargs: dict, solve_kwargs: dict):
+        gfm.assemble(alpha.detach(), phi.detach(), **phys_kwargs)
+        p, _, info = gfm.solve(**solve_kwargs)
+        ctx.gfm = gfm
+        ctx.phys_kwargs = phys_kwargs
+        ctx.solve_kwargs = solve_kwargs
+        ctx.save_for_backward(alpha.detach(), phi.detach(), p)
+        ctx.stamp = id(gfm.phys)
+        return p
+
+    @staticmethod
+    def backward(ctx, grad_p):
+        alpha, phi, p = ctx.saved_tensors
+        gfm = ctx.gfm
+        if id(gfm.phys) != ctx.stamp:
+            gfm.assemble(alpha, phi, **ctx.phys_kwargs)
+        kw = dict(mode=ctx.solve_kwargs.get("mode", "fp64"), rtol=min(ctx.solve_kwargs.get("rtol", 1e-10), 1e-10))
+        dphi, dalpha, _, _ = gfm.adjoint(p, grad_p.contiguous(), **kw)
+        return dalpha, dphi, None, None, None

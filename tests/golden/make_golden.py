@@ -3,7 +3,9 @@
 Run:  python tests/golden/make_golden.py
 Each fixture is a small case from ``cases`` solved by the CPU oracle
 (dense Cholesky), stored as hex floats so the per-face quantities can be
-compared bit for bit.
+compared bit for bit.  The inputs (alpha, phi) are stored too: the case
+generator calls libm (cos, cosh), whose last bits differ between machines,
+so tests read the stored inputs instead of regenerating them.
 """
 import os
 import sys
@@ -29,12 +31,12 @@ def write(name, c):
     with open(path, "w") as fh:
         fh.write(f"# {name}: oracle output (dense Cholesky) for cases recipe {name}\n")
         fh.write(f"# n {c.n} F {c.F} ref_cell {c.ref_cell}\n")
-        fh.write("# face: f lambda gamma jump corrected_flux (hex floats)\n")
+        fh.write("# face: f phi lambda gamma jump corrected_flux (hex floats)\n")
         for f in range(c.F):
-            fh.write(f"F {f} {fc.lam[f].hex()} {fc.gamma[f].hex()} {fc.jump[f].hex()} {q[f].hex()}\n")
-        fh.write("# cell: i diag b p (hex floats)\n")
+            fh.write(f"F {f} {c.phi[f].hex()} {fc.lam[f].hex()} {fc.gamma[f].hex()} {fc.jump[f].hex()} {q[f].hex()}\n")
+        fh.write("# cell: i alpha diag b p (hex floats)\n")
         for i in range(c.n):
-            fh.write(f"C {i} {sy.diag[i].hex()} {sy.b[i].hex()} {p[i].hex()}\n")
+            fh.write(f"C {i} {c.alpha[i].hex()} {sy.diag[i].hex()} {sy.b[i].hex()} {p[i].hex()}\n")
 
 
 def read(name):
@@ -47,7 +49,17 @@ def read(name):
             vals = [float.fromhex(v) for v in t[2:]]
             (faces if t[0] == "F" else cells).append(vals)
     fa, ca = np.array(faces), np.array(cells)
-    return dict(lam=fa[:, 0], gamma=fa[:, 1], jump=fa[:, 2], flux=fa[:, 3], diag=ca[:, 0], b=ca[:, 1], p=ca[:, 2])
+    return {"phi": fa[:, 0], "lam": fa[:, 1], "lambda": fa[:, 1], "gamma": fa[:, 2], "jump": fa[:, 3],
+            "flux": fa[:, 4], "alpha": ca[:, 0], "diag": ca[:, 1], "b": ca[:, 2], "p": ca[:, 3]}
+
+
+def case(name):
+    """The fixture's case with its stored inputs (machine independent)."""
+    c = FIXTURES[name]()
+    g = read(name)
+    c.alpha = g["alpha"].copy()
+    c.phi = g["phi"].copy()
+    return c, g
 
 
 if __name__ == "__main__":

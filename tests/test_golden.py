@@ -15,8 +15,7 @@ import oracle  # noqa: E402
 
 @pytest.mark.parametrize("name", sorted(make_golden.FIXTURES))
 def test_oracle_reproduces_golden(name):
-    c = make_golden.FIXTURES[name]()
-    gold = make_golden.read(name)
+    c, gold = make_golden.case(name)
     p, fc, sy, _ = oracle.solve(c, direct=True)
     assert np.array_equal(fc.lam, gold["lam"])
     assert np.array_equal(fc.gamma, gold["gamma"])
