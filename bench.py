@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6800.0
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gfm", "reference"], default="gfm")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample length")

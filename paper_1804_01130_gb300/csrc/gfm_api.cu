@@ -436,10 +436,14 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     ca.dinv32 = h->dinv32;
     ca.prm = h->prm;
     GFM_CUDA(h, gfm::launch_cells(ca, s));
-    GFM_CUDA(h, gfm::launch_bsums(h->b, h->n, h->prm, s));
+    int launched = 2;
+    if (h->ref_internal < 0) {  // only an unpinned system needs sum(b) for its compatibility test
+        GFM_CUDA(h, gfm::launch_bsums(h->b, h->n, h->prm, s));
+        ++launched;
+    }
     prof_record(h, 1, s);
-    h->prof.launches += 3;
-    h->prof.launches_total += 3;
+    h->prof.launches += launched;
+    h->prof.launches_total += launched;
     h->assembled = true;
     return GFM_OK;
 }
