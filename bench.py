@@ -53,6 +53,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--profile-run", choices=["tank2d", "box3d"], default=None,
+                    help="no timing: one short mixed and one short FP64 solve for a profiler")
+    ap.add_argument("--profile-iters", type=int, default=300)
     return ap.parse_args()
 
 
@@ -366,8 +369,28 @@ def run_gfm(args, rank, local, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_run(args):
+    """One short mixed and one short FP64 solve (max_iters capped), no timing:
+    the program an external profiler (ncu) wraps."""
+    import torch
+
+    import cases
+    import paper_1804_01130_gb300 as g
+    case = cases.make_case(2 if args.profile_run == "tank2d" else 3)
+    s = g.GFM.from_case(case, renumber=1)
+    s.assemble(torch.as_tensor(case.alpha), torch.as_tensor(case.phi), case.rho_w, case.rho_a, case.g,
+               case.ref_cell)
+    for mode in ("mixed", "fp64"):
+        _, _, info = s.solve(mode=mode, rtol=1e-10, max_iters=args.profile_iters, raise_on_error=False)
+        print(mode, info, flush=True)
+    torch.cuda.synchronize()
+
+
 def main():
     args = _args()
+    if args.profile_run:
+        profile_run(args)
+        return
     rank, local, world = _dist()
     if args.impl == "reference":
         run_reference(args, rank, world)

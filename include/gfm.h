@@ -142,7 +142,7 @@ typedef struct {
 
 /* Launch shape of the persistent solver kernels (autotuned or set). */
 typedef struct {
-    int32_t threads;     /* threads per CTA (multiple of 32, <= 1024)       */
+    int32_t threads;     /* threads per CTA (multiple of 32, <= 512)        */
     int32_t ctas_per_sm; /* co-resident CTAs per SM (grid = SMs x this)     */
 } gfm_tuning;
 
@@ -172,6 +172,22 @@ gfm_status gfm_default_opts(gfm_solve_opts *opts);
  * GFM_ERR_NOMEM, GFM_ERR_CUDA.
  */
 gfm_status gfm_create(const gfm_mesh *mesh, int32_t renumber, gfm_stream stream, gfm_handle *out);
+
+/*
+ * Batched handle: n_tanks (<= 128) independent meshes ("tanks", e.g. many
+ * wave tanks of uneven size) solved together by ONE persistent launch.  All
+ * later cell and face arrays are the tanks' arrays concatenated in tank
+ * order; gfm_assemble's `phys` is then a host array of n_tanks entries, each
+ * ref_cell numbered within its tank and >= 0.  gfm_solve runs GFM_MIXED only:
+ * every tank keeps its own CG scalars, residual replacements and stopping
+ * test, finished tanks drop out while the others iterate, and `info` points
+ * to n_tanks records (the returned status is the last failing tank's).  The
+ * launch needs at least one CTA per tank.  The adjoint and the host-buffer
+ * entry point take single-mesh handles; batched tanks use the Jacobi
+ * preconditioner (no coarse space).  Errors as gfm_create.
+ */
+gfm_status gfm_create_batched(const gfm_mesh *meshes, int32_t n_tanks, int32_t renumber, gfm_stream stream,
+                              gfm_handle *out);
 
 /* Release the handle and its device workspace (synchronises the device). */
 gfm_status gfm_destroy(gfm_handle h);
@@ -235,10 +251,28 @@ gfm_status gfm_solve_adjoint(gfm_handle h, const gfm_solve_opts *opts, const dou
 gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *phi_host, const gfm_phys *phys,
                           const gfm_solve_opts *opts, double *p_host, gfm_solve_info *info, gfm_stream stream);
 
-/* Launch shape of the persistent kernels.  threads = 0 / ctas_per_sm = 0 keep
- * the current value.  Errors: GFM_ERR_ARG if the shape cannot be co-resident. */
+/* Launch shape of the persistent kernels (threads a multiple of 32, at most
+ * 512).  threads = 0 / ctas_per_sm = 0 keep the current value.  Errors:
+ * GFM_ERR_ARG if the shape is out of range or cannot be co-resident. */
 gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t);
 gfm_status gfm_get_tuning(gfm_handle h, gfm_tuning *t);
+
+/*
+ * Two-level preconditioner.  With a density ratio of 1000 the ghost-fluid
+ * Laplacian (Sec. 3.1) couples each connected region of one phase to the rest
+ * only through its interface faces, and Jacobi-PCG stalls for thousands of
+ * iterations on the near-constant modes of the large regions.  Every
+ * assembly finds the connected regions of each phase (cells joined by
+ * non-interface faces) and keeps the up-to-max_vectors largest with at least
+ * min_size cells as coarse space Z; the preconditioner is then
+ * D^{-1} + Z (Z^T A Z)^{-1} Z^T.  max_vectors = 0 gives plain Jacobi.
+ * Defaults: 8 vectors, 64 cells.  Takes effect at the next gfm_assemble.
+ * The coarse space needs a pin (ref_cell >= 0); unpinned systems use Jacobi.
+ * gfm_get_coarse reports (host pointers, synchronises `stream`) the vectors in
+ * use, the regions of at least min_size cells, and the sizes [8] of the kept ones.
+ */
+gfm_status gfm_set_coarse(gfm_handle h, int32_t max_vectors, int32_t min_size);
+gfm_status gfm_get_coarse(gfm_handle h, int32_t *n_vectors, int32_t *n_regions, int32_t *sizes, gfm_stream stream);
 
 /* Profiling: on = 1 records CUDA events around every kernel of each call. */
 gfm_status gfm_set_profiling(gfm_handle h, int32_t on);

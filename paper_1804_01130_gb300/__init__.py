@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "GFMError", "SolveInfo", "Profile", "GFM", "GFMSolve", "load_library", "library_path",
+    "GFMError", "SolveInfo", "Profile", "GFM", "GFMBatch", "GFMSolve", "load_library", "library_path",
     "GFM_OK", "GFM_ERR_ARG", "GFM_ERR_CUDA", "GFM_ERR_NOMEM", "GFM_ERR_NOT_CONVERGED", "GFM_ERR_BREAKDOWN",
     "GFM_ERR_TIMEOUT", "GFM_ERR_INCOMPATIBLE", "GFM_ERR_STATE", "EXPORTED_SYMBOLS",
 ]
@@ -31,6 +31,7 @@ EXPORTED_SYMBOLS = (
     "gfm_default_opts", "gfm_create", "gfm_destroy", "gfm_assemble", "gfm_export_system", "gfm_solve",
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
+    "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched",
 )
 
 
@@ -111,6 +112,7 @@ def load_library(build_if_missing: bool = True):
     sig = {
         "gfm_default_opts": ([ct.POINTER(_Opts)], S),
         "gfm_create": ([ct.POINTER(_Mesh), I, P, ct.POINTER(P)], S),
+        "gfm_create_batched": ([P, I, I, P, ct.POINTER(P)], S),
         "gfm_destroy": ([P], S),
         "gfm_assemble": ([P, P, P, ct.POINTER(_Phys), P], S),
         "gfm_export_system": ([P, P, P, P, P, P, P], S),
@@ -123,6 +125,8 @@ def load_library(build_if_missing: bool = True):
         "gfm_get_profile": ([P, ct.POINTER(_Profile)], S),
         "gfm_get_sizes": ([P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)], S),
         "gfm_get_permutation": ([P, P], S),
+        "gfm_set_coarse": ([P, I, I], S),
+        "gfm_get_coarse": ([P, ct.POINTER(I), ct.POINTER(I), P, P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
     }
@@ -308,6 +312,19 @@ class GFM:
         self._check(self.lib.gfm_get_tuning(self.h, ct.byref(t)), "gfm_get_tuning")
         return t.threads, t.ctas_per_sm
 
+    def set_coarse(self, max_vectors: int = 8, min_size: int = 64):
+        """Coarse space of the two-level preconditioner (0 vectors = Jacobi only); next assembly on."""
+        self._check(self.lib.gfm_set_coarse(self.h, int(max_vectors), int(min_size)), "gfm_set_coarse")
+
+    def coarse_info(self, stream=None):
+        """(vectors in use, regions of at least min_size cells, sizes of the kept regions)."""
+        import numpy as np
+        k, nr = ct.c_int32(), ct.c_int32()
+        sizes = np.zeros(8, dtype=np.int32)
+        self._check(self.lib.gfm_get_coarse(self.h, ct.byref(k), ct.byref(nr), ct.c_void_p(sizes.ctypes.data),
+                                            _stream(stream)), "gfm_get_coarse")
+        return k.value, nr.value, sizes[:k.value].tolist()
+
     def set_profiling(self, on: bool = True):
         self._check(self.lib.gfm_set_profiling(self.h, int(bool(on))), "gfm_set_profiling")
 
@@ -359,3 +376,81 @@ class GFMSolve(torch.autograd.Function):
         kw = dict(mode=ctx.solve_kwargs.get("mode", "fp64"), rtol=min(ctx.solve_kwargs.get("rtol", 1e-10), 1e-10))
         dphi, dalpha, _, _ = gfm.adjoint(p, grad_p.contiguous(), **kw)
         return dalpha, dphi, None, None, None
+
+
+class GFMBatch(GFM):
+    """Many independent tanks solved by one persistent launch (gfm_create_batched).
+
+    ``tanks`` is a list of objects with owner, neighbour, Sf, C (e.g. cases.Case).
+    Cell and face arrays of every later call are the tanks' arrays concatenated
+    in tank order; physics is given per tank.
+    """
+
+    def __init__(self, tanks, renumber: int = 1, device=None, stream=None):
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise GFMError(GFM_ERR_CUDA, "no CUDA device: libgfm has no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        d = self.device
+        self.T = len(tanks)
+        self._keep = []
+        meshes = (_Mesh * self.T)()
+        self.ncell, self.nface = [], []
+        for k, t in enumerate(tanks):
+            own, nb = _i32(t.owner, d), _i32(t.neighbour, d)
+            Sf = _f64(t.Sf, d).reshape(3, -1).contiguous()
+            C = _f64(t.C, d).reshape(3, -1).contiguous()
+            self._keep += [own, nb, Sf, C]
+            meshes[k] = _Mesh(int(C.shape[1]), int(own.numel()), own.data_ptr(), nb.data_ptr(), Sf.data_ptr(),
+                              C.data_ptr(), None)
+            self.ncell.append(int(C.shape[1]))
+            self.nface.append(int(own.numel()))
+        h = ct.c_void_p()
+        with torch.cuda.device(d):
+            st = self.lib.gfm_create_batched(ct.cast(meshes, ct.c_void_p), self.T, int(renumber), _stream(stream),
+                                             ct.byref(h))
+        if st != GFM_OK:
+            raise GFMError(st, f"gfm_create_batched: {self.lib.gfm_status_string(st).decode()}")
+        self._keep = []  # the handle holds its own copy of the meshes
+        self.h = h
+        self.n = sum(self.ncell)
+        self.F = sum(self.nface)
+        self.phys = None
+        self._info_dev = torch.zeros(4 * self.T, dtype=torch.float64, device=d)
+
+    def assemble(self, alpha, phi, phys: list, stream=None):
+        """phys: list of dicts (rho_w, rho_a, g, ref_cell, ref_value), one per tank."""
+        alpha = _f64(alpha, self.device)
+        phi = _f64(phi, self.device)
+        arr = (_Phys * self.T)()
+        for k, ph in enumerate(phys):
+            arr[k] = self.make_phys(**ph)
+        self.phys = arr
+        self._check(self.lib.gfm_assemble(self.h, _ptr(alpha), _ptr(phi), ct.cast(arr, ct.POINTER(_Phys)),
+                                          _stream(stream)), "gfm_assemble")
+
+    def solve(self, mode="mixed", rtol=1e-8, inner_rtol=1e-4, p0=None, phi_corr=False, max_iters=1_000_000,
+              max_refine=30, info_on_device=False, timeout_ms=2000.0, out=None, raise_on_error=True, stream=None):
+        """Returns (p, phi_corr or None, list of SolveInfo or the device records)."""
+        p = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=self.device)
+        if p0 is not None:
+            p.copy_(_f64(p0, self.device))
+        fc = torch.empty(self.F, dtype=torch.float64, device=self.device) if phi_corr else None
+        o = self.make_opts(mode, rtol, inner_rtol, max_iters, max_refine, p0 is not None, info_on_device, timeout_ms)
+        if info_on_device:
+            st = self.lib.gfm_solve(self.h, ct.byref(o), _ptr(p), _ptr(fc), _ptr(self._info_dev), _stream(stream))
+            self._check(st, "gfm_solve")
+            return p, fc, self._info_dev
+        infos = (_Info * self.T)()
+        st = self.lib.gfm_solve(self.h, ct.byref(o), _ptr(p), _ptr(fc), ct.cast(infos, ct.c_void_p),
+                                _stream(stream))
+        out_infos = [SolveInfo(i.iters, i.refinements, i.status, i.rel_res_l2, i.rel_res_l1) for i in infos]
+        if st != GFM_OK and (raise_on_error or st not in (GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN,
+                                                          GFM_ERR_TIMEOUT)):
+            self._check(st, "gfm_solve")
+        return p, fc, out_infos
+
+    def infos_from_device(self, t: torch.Tensor):
+        raw = t.detach().cpu().numpy().tobytes()
+        rec = (_Info * self.T).from_buffer_copy(raw)
+        return [SolveInfo(i.iters, i.refinements, i.status, i.rel_res_l2, i.rel_res_l1) for i in rec]

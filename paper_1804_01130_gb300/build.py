@@ -25,6 +25,7 @@ UNITS = {
     "gfm_api.cu": [],
     "gfm_assemble.cu": ["--fmad=false"],
     "gfm_solve.cu": ["-Xptxas", "-v"],
+    "gfm_coarse.cu": [],
     "gfm_setup.cpp": [],
 }
 HEADERS = ["gfm_internal.h", "gfm_setup.h"]

@@ -1,5 +1,6 @@
 // C ABI of libgfm (include/gfm.h): handle lifetime, argument checks, device
 // workspace, launches of the assembly and solver kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 struct gfm_ctx {
     int device = 0;
     int sm_count = 0;
+    int smem_per_sm = 0, smem_optin = 0;
     int n = 0, F = 0;
     gfm::HostTables ht;
     // caller-order mesh copies
@@ -33,6 +35,23 @@ struct gfm_ctx {
     double *p64 = nullptr, *q64 = nullptr, *rhs = nullptr, *tmp_user = nullptr, *tmp_user2 = nullptr;
     float2 *UP0 = nullptr, *UP1 = nullptr;
     float *R32 = nullptr, *S32 = nullptr, *E = nullptr, *dinv32 = nullptr;
+    // two-level preconditioner (coarse space of connected one-phase regions)
+    int32_t *cc_parent = nullptr, *cc_size = nullptr, *cc_cand = nullptr, *cc_counters = nullptr;
+    int8_t *comp = nullptr;
+    gfm::CrossFace *cross = nullptr;
+    gfm::Coarse *coarse = nullptr;
+    int max_cross = 0;
+    int coarse_max = gfm::kMaxCoarse, coarse_min_size = 64;
+    // batch of tanks (gfm_create_batched)
+    bool batched = false;
+    int T = 0, cta_grid = 0;
+    gfm::BatchTables bt;
+    int32_t *ftank = nullptr, *stank = nullptr, *tncell = nullptr;
+    gfm::TankPhys *tphys = nullptr, *tphys_h = nullptr;
+    gfm::DevParams *tprm = nullptr, *tprm_h = nullptr;
+    int4 *cta = nullptr;
+    int2 *tank_cta = nullptr;
+    gfm_solve_info *binfos = nullptr, *binfos_h = nullptr;
     // host-buffer entry point staging
     double *stage_alpha = nullptr, *stage_phi = nullptr, *stage_p = nullptr;
     // control
@@ -51,6 +70,7 @@ struct gfm_ctx {
     bool profiling = false;
     gfm_profile prof{};
     cudaEvent_t ev[6] = {};
+    bool ev_recorded[6] = {};
     std::string last_error;
 };
 
@@ -86,10 +106,14 @@ void free_all(gfm_ctx *h)
                     h->val64, h->val32, h->lambda, h->gamma, h->jump, h->sigma, h->phi, h->dl_dlam, h->kind,
                     h->alpha, h->b, h->diag, h->dinv, h->x64, h->r64, h->p64, h->q64, h->rhs, h->tmp_user,
                     h->tmp_user2, h->UP0, h->UP1, h->R32, h->S32, h->E, h->dinv32, h->stage_alpha, h->stage_phi, h->stage_p, h->prm, h->bar,
-                    h->err, h->partials, h->dinfo};
+                    h->err, h->partials, h->dinfo, h->cc_parent, h->cc_size, h->cc_cand, h->cc_counters,
+                    h->comp, h->cross, h->coarse, h->ftank, h->stank, h->tncell, h->tphys, h->tprm, h->cta,
+                    h->tank_cta, h->binfos};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    if (h->hinfo) cudaFreeHost(h->hinfo);
+    void *hptrs[] = {h->hinfo, h->tphys_h, h->tprm_h, h->binfos_h};
+    for (void *p : hptrs)
+        if (p) cudaFreeHost(p);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -121,23 +145,91 @@ gfm_status check_opts(gfm_ctx *h, const gfm_solve_opts *o)
     return GFM_OK;
 }
 
-gfm_status grid_shape(gfm_ctx *h, gfm::Mode mode, int *grid, int *threads)
+// Launch shape of a persistent solve and its shared-memory staging of the
+// slice tables: each CTA keeps its slices' (base, width) and as many of its
+// slots (neighbour + coefficient) as fit next to the other CTAs of its SM.
+struct LaunchPlan {
+    int grid = 0, threads = 0, cache_cap = 0, meta_slots = 0;
+    size_t dyn = 0;
+};
+
+gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
 {
-    int t = h->tuning.threads, per = h->tuning.ctas_per_sm;
+    const int t = h->tuning.threads;
+    int per = h->tuning.ctas_per_sm;
+    const void *k = h->batched ? gfm::batched_kernel(h->ht.max_width) : gfm::solver_kernel(mode, h->ht.max_width, t);
+    cudaFuncAttributes fa;
+    GFM_CUDA(h, cudaFuncGetAttributes(&fa, k));
+    int occ0 = 0;
+    GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k, t, 0));
+    if (occ0 < 1) return fail(h, GFM_ERR_ARG, "solver kernel cannot run with this many threads per CTA");
+    if (per > occ0) per = occ0;
+    int grid = h->sm_count * per;
+    if (grid > h->max_grid) grid = h->max_grid;
+    // per-CTA budget: the SM's shared memory split between its CTAs
+    long long budget = (long long)h->smem_per_sm / per - (long long)fa.sharedSizeBytes - 1024;
+    budget = std::min<long long>(budget, (long long)h->smem_optin - (long long)fa.sharedSizeBytes);
+    if (budget < 0) budget = 0;
+    const int ns = h->ht.n_slices;
+    int max_nsl = 0, max_slots = 0;
+    if (h->batched) {
+        if (h->cta_grid != grid) return fail(h, GFM_ERR_STATE, "batched CTA table out of date");
+        std::vector<int32_t> cta4, tank2;
+        std::string err;
+        if (!gfm::plan_batch_ctas(h->bt, grid, cta4, tank2, err)) return fail(h, GFM_ERR_ARG, err);
+        for (int b = 0; b < grid; ++b) {
+            const int s0 = cta4[(size_t)b * 4 + 1], s1 = cta4[(size_t)b * 4 + 2];
+            max_nsl = std::max(max_nsl, s1 - s0);
+            max_slots = std::max(max_slots, h->ht.slice_ptr[(size_t)s1] - h->ht.slice_ptr[(size_t)s0]);
+        }
+    } else {
+        for (int b = 0; b < grid; ++b) {
+            const int s0 = (int)(((long long)ns * b) / grid), s1 = (int)(((long long)ns * (b + 1)) / grid);
+            max_nsl = std::max(max_nsl, s1 - s0);
+            max_slots = std::max(max_slots, h->ht.slice_ptr[(size_t)s1] - h->ht.slice_ptr[(size_t)s0]);
+        }
+    }
+    const int meta_slots = (max_nsl + 1) & ~1;
+    const long long meta_bytes = (long long)meta_slots * 8;
+    const long long slot_bytes = 4 + (mode == gfm::Mode::FP64 ? 8 : 4);
+    long long cap = budget > meta_bytes ? (budget - meta_bytes) / slot_bytes : 0;
+    cap = std::min<long long>(cap, max_slots);
+    cap &= ~3LL;
+    if (meta_bytes > budget) return fail(h, GFM_ERR_ARG, "mesh too large for this launch shape");
+    const size_t dyn = (size_t)(meta_bytes + cap * slot_bytes);
+    GFM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int occ = 0;
-    GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gfm::solver_kernel(mode, h->ht.max_width, t), t, 0));
-    if (occ < 1) return fail(h, GFM_ERR_ARG, "solver kernel cannot run with this many threads per CTA");
-    if (per > occ) per = occ;
-    *grid = h->sm_count * per;
-    if (*grid > h->max_grid) *grid = h->max_grid;
-    *threads = t;
+    GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, t, dyn));
+    if (occ < per) return fail(h, GFM_ERR_ARG, "launch shape cannot be co-resident with its shared-memory staging");
+    lp->grid = grid;
+    lp->threads = t;
+    lp->cache_cap = (int)cap;
+    lp->meta_slots = meta_slots;
+    lp->dyn = dyn;
     return GFM_OK;
 }
 
 void prof_record(gfm_ctx *h, int k, cudaStream_t s)
 {
-    if (h->profiling) cudaEventRecord(h->ev[k], s);
+    if (h->profiling && cudaEventRecord(h->ev[k], s) == cudaSuccess) h->ev_recorded[k] = true;
 }
+
+// Elapsed time between two recorded events, 0 otherwise; never leaves a
+// sticky runtime error behind.
+float prof_elapsed(gfm_ctx *h, int a, int b)
+{
+    float ms = 0.0f;
+    if (!h->ev_recorded[a] || !h->ev_recorded[b]) return 0.0f;
+    if (cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0.0f;
+    }
+    return ms;
+}
+
+// Entry of every call that launches work: drop a stale error left by code
+// outside the library so that it is not reported as this call's failure.
+void clear_stale_error() { (void)cudaGetLastError(); }
 
 // Enqueue one persistent solve of A x = rhs (internal order) writing the
 // solution in caller order to out_user.  info_dev receives the result.
@@ -145,9 +237,10 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
                          gfm_solve_info *info_dev, cudaStream_t s)
 {
     const gfm::Mode mode = (o->mode == GFM_MIXED) ? gfm::Mode::MIXED : gfm::Mode::FP64;
-    int grid = 0, threads = 0;
-    gfm_status st = grid_shape(h, mode, &grid, &threads);
+    LaunchPlan lp;
+    gfm_status st = plan_launch(h, mode, &lp);
     if (st != GFM_OK) return st;
+    const int grid = lp.grid, threads = lp.threads;
     GFM_CUDA(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), s));
     GFM_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), s));
     GFM_CUDA(h, cudaMemsetAsync(info_dev, 0, sizeof(gfm_solve_info), s));
@@ -175,13 +268,31 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
     a.max_refine = o->max_refine;
     a.use_x0 = use_x0;
     a.budget_ns = (unsigned long long)(o->timeout_ms * 1e6);
+    a.coarse = h->coarse;
+    a.comp = h->comp;
+    a.cross = h->cross;
+    a.cache_cap = lp.cache_cap;
+    a.meta_slots = lp.meta_slots;
     a.bar = h->bar;
     a.err = h->err;
     a.partials = h->partials;
     a.info = info_dev;
-    void *args[] = {&a};
+    gfm::BatchArgs ba{};
+    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads);
+    if (h->batched) {
+        a.n_per_tank = h->tncell;
+        a.prm = h->tprm;
+        ba.T = h->T;
+        ba.cta = h->cta;
+        ba.tank_cta = h->tank_cta;
+        ba.tprm = h->tprm;
+        ba.infos = info_dev;
+        kernel = gfm::batched_kernel(h->ht.max_width);
+        GFM_CUDA(h, cudaMemsetAsync(info_dev, 0, sizeof(gfm_solve_info) * h->T, s));
+    }
+    void *args[] = {&a, &ba};
     prof_record(h, 2, s);
-    GFM_CUDA(h, cudaLaunchCooperativeKernel(gfm::solver_kernel(mode, h->ht.max_width, threads), dim3(grid), dim3(threads), args, 0, s));
+    GFM_CUDA(h, cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(threads), args, lp.dyn, s));
     prof_record(h, 3, s);
     h->prof.grid = grid;
     h->prof.threads = threads;
@@ -193,12 +304,31 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
 gfm_status finish_info(gfm_ctx *h, const gfm_solve_opts *o, gfm_solve_info *info, cudaStream_t s)
 {
     if (o->info_on_device) return GFM_OK;
+    if (h->batched) {
+        GFM_CUDA(h, cudaMemcpyAsync(h->binfos_h, h->binfos, sizeof(gfm_solve_info) * h->T, cudaMemcpyDeviceToHost, s));
+        GFM_CUDA(h, cudaStreamSynchronize(s));
+        if (info) std::memcpy(info, h->binfos_h, sizeof(gfm_solve_info) * h->T);
+        if (h->profiling) {
+            h->prof.ms_solve = prof_elapsed(h, 2, 3);
+            h->prof.ms_total = prof_elapsed(h, 4, 5);
+        }
+        gfm_status worst = GFM_OK;
+        for (int t = 0; t < h->T; ++t)
+            if (h->binfos_h[t].status != GFM_OK) {
+                worst = (gfm_status)h->binfos_h[t].status;
+                char buf[160];
+                snprintf(buf, sizeof buf, "tank %d ended with %s after %d iterations", t, gfm_status_string(worst),
+                         h->binfos_h[t].iters);
+                h->last_error = buf;
+            }
+        return worst;
+    }
     GFM_CUDA(h, cudaMemcpyAsync(h->hinfo, h->dinfo, sizeof(gfm_solve_info), cudaMemcpyDeviceToHost, s));
     GFM_CUDA(h, cudaStreamSynchronize(s));
     if (info) *info = *h->hinfo;
     if (h->profiling) {
-        cudaEventElapsedTime(&h->prof.ms_solve, h->ev[2], h->ev[3]);
-        cudaEventElapsedTime(&h->prof.ms_total, h->ev[4], h->ev[5]);
+        h->prof.ms_solve = prof_elapsed(h, 2, 3);
+        h->prof.ms_total = prof_elapsed(h, 4, 5);
     }
     const gfm_status st = (gfm_status)h->hinfo->status;
     if (st != GFM_OK) {
@@ -219,6 +349,109 @@ gfm_status check_compat(gfm_ctx *h, cudaStream_t s)
     GFM_CUDA(h, cudaStreamSynchronize(s));
     if (fabs(p.bsum) > 1e-12 * p.babs)
         return fail(h, GFM_ERR_INCOMPATIBLE, "unpinned system with incompatible source (sum(b) != 0)");
+    return GFM_OK;
+}
+
+gfm_status init_device(gfm_ctx *h)
+{
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess)
+        return fail(h, GFM_ERR_CUDA, "no CUDA device");
+    return GFM_OK;
+}
+
+// Device workspace and the mesh tables (h->n, h->F, h->ht set).
+gfm_status alloc_upload(gfm_ctx *h, cudaStream_t s)
+{
+    const int n = h->n, F = h->F;
+    const size_t np = (size_t)h->ht.n_pad, ns = (size_t)h->ht.n_slots;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gfm::solver_kernel(gfm::Mode::MIXED, h->ht.max_width, 32), 32, 0);
+    h->max_grid = h->sm_count * (occ > 0 ? occ : 1);
+    cudaError_t e = cudaSuccess;
+#define A(ptr, cnt) \
+    if (e == cudaSuccess) e = dalloc(&h->ptr, (cnt))
+    A(owner, F); A(neighbour, F); A(Sf, 3 * (size_t)F); A(C, 3 * (size_t)n);
+    A(perm, n); A(iperm, np); A(slice_ptr, (size_t)h->ht.n_slices + 1); A(col, ns); A(face, ns);
+    A(val64, ns); A(val32, ns);
+    A(lambda, F); A(gamma, F); A(jump, F); A(sigma, F); A(phi, F); A(dl_dlam, F); A(kind, F);
+    A(alpha, n); A(b, np); A(diag, np); A(dinv, np); A(x64, np); A(r64, np); A(p64, np); A(q64, np);
+    A(rhs, np); A(tmp_user, n); A(tmp_user2, n); A(UP0, np); A(UP1, np); A(R32, np); A(S32, np); A(E, np);
+    A(dinv32, np);
+    A(stage_alpha, n); A(stage_phi, F); A(stage_p, n);
+    A(prm, 1); A(bar, 1); A(err, 1); A(partials, 2 * (size_t)h->max_grid * 12); A(dinfo, 1);
+    h->max_cross = (int)std::min<long long>((long long)F, std::max<long long>(65536, (long long)F / 8));
+    A(cc_parent, n); A(cc_size, n); A(cc_cand, gfm::kMaxCandidates); A(cc_counters, 2);
+    A(comp, np); A(cross, h->max_cross); A(coarse, 1);
+#undef A
+    if (e != cudaSuccess)
+        return fail(h, e == cudaErrorMemoryAllocation ? GFM_ERR_NOMEM : GFM_ERR_CUDA,
+                    std::string("device allocation: ") + cudaGetErrorString(e));
+    if (cudaMallocHost((void **)&h->hinfo, sizeof(gfm_solve_info)) != cudaSuccess)
+        return fail(h, GFM_ERR_NOMEM, "pinned host allocation");
+    for (auto &ev : h->ev) cudaEventCreate(&ev);
+    e = cudaMemcpyAsync(h->perm, h->ht.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->iperm, h->ht.iperm.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->slice_ptr, h->ht.slice_ptr.data(), sizeof(int32_t) * (h->ht.n_slices + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->col, h->ht.col.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->face, h->ht.face.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s);
+    // zero every vector once so padding lanes hold finite values
+    double *zero_d[] = {h->b, h->diag, h->dinv, h->x64, h->r64, h->p64, h->q64, h->rhs};
+    for (double *zp : zero_d)
+        if (e == cudaSuccess) e = cudaMemsetAsync(zp, 0, sizeof(double) * np, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->comp, 0xff, np, s);  // -1: no coarse region
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->coarse, 0, sizeof(gfm::Coarse), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->UP0, 0, sizeof(float2) * np, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->UP1, 0, sizeof(float2) * np, s);
+    float *zero_f[] = {h->R32, h->S32, h->E, h->dinv32};
+    for (float *zp : zero_f)
+        if (e == cudaSuccess) e = cudaMemsetAsync(zp, 0, sizeof(float) * np, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "uploading tables");
+    return GFM_OK;
+}
+
+// Batch-only workspace: tank of every face and slice, per-tank physics,
+// pins, cell counts and results, CTA table.
+gfm_status alloc_batch(gfm_ctx *h, cudaStream_t s)
+{
+    const int T = h->T;
+    cudaError_t e = dalloc(&h->ftank, (size_t)h->F);
+    if (e == cudaSuccess) e = dalloc(&h->stank, (size_t)h->ht.n_slices);
+    if (e == cudaSuccess) e = dalloc(&h->tphys, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&h->tprm, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&h->tncell, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&h->cta, (size_t)h->max_grid);
+    if (e == cudaSuccess) e = dalloc(&h->tank_cta, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&h->binfos, (size_t)T);
+    if (e != cudaSuccess) return fail(h, GFM_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+    if (cudaMallocHost((void **)&h->tphys_h, sizeof(gfm::TankPhys) * T) != cudaSuccess ||
+        cudaMallocHost((void **)&h->tprm_h, sizeof(gfm::DevParams) * T) != cudaSuccess ||
+        cudaMallocHost((void **)&h->binfos_h, sizeof(gfm_solve_info) * T) != cudaSuccess)
+        return fail(h, GFM_ERR_NOMEM, "pinned host allocation");
+    e = cudaMemcpyAsync(h->ftank, h->bt.face_tank.data(), sizeof(int32_t) * h->F, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->stank, h->bt.slice_tank.data(), sizeof(int32_t) * h->ht.n_slices, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tncell, h->bt.ncell.data(), sizeof(int32_t) * T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "uploading batch tables");
+    return GFM_OK;
+}
+
+// CTA table of the batched solve for the current launch shape (synchronous).
+gfm_status plan_batch(gfm_ctx *h)
+{
+    if (!h->batched) return GFM_OK;
+    const int grid = std::min(h->sm_count * h->tuning.ctas_per_sm, h->max_grid);
+    std::vector<int32_t> cta4, tank2;
+    std::string err;
+    if (!gfm::plan_batch_ctas(h->bt, grid, cta4, tank2, err)) return fail(h, GFM_ERR_ARG, err);
+    cudaError_t e = cudaMemcpy(h->cta, cta4.data(), sizeof(int32_t) * cta4.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->tank_cta, tank2.data(), sizeof(int32_t) * tank2.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "uploading the CTA table");
+    h->cta_grid = grid;
     return GFM_OK;
 }
 
@@ -267,107 +500,158 @@ gfm_status gfm_create(const gfm_mesh *mesh, int32_t renumber, gfm_stream stream,
     if (renumber < 0 || renumber > 2) return GFM_ERR_ARG;
     gfm_ctx *h = new (std::nothrow) gfm_ctx();
     if (!h) return GFM_ERR_NOMEM;
+    clear_stale_error();
     cudaStream_t s = (cudaStream_t)stream;
     const int n = mesh->n_cells, F = mesh->n_faces;
     h->n = n;
     h->F = F;
-    gfm_status st = GFM_OK;
+    gfm_status st = init_device(h);
     do {
-        if (cudaGetDevice(&h->device) != cudaSuccess ||
-            cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
-            st = GFM_ERR_CUDA;
-            h->last_error = "no CUDA device";
-            break;
-        }
+        if (st != GFM_OK) break;
         std::vector<int32_t> ho((size_t)F), hn((size_t)F);
         std::vector<double> hC;
         if (cudaMemcpyAsync(ho.data(), mesh->owner, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaMemcpyAsync(hn.data(), mesh->neighbour, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess) {
-            st = GFM_ERR_CUDA;
-            h->last_error = "reading owner/neighbour (must be device pointers)";
+            st = fail(h, GFM_ERR_CUDA, "reading owner/neighbour (must be device pointers)");
             break;
         }
         if (renumber == 2) {
             hC.resize((size_t)3 * n);
             if (cudaMemcpyAsync(hC.data(), mesh->C, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess) {
-                st = GFM_ERR_CUDA;
-                h->last_error = "reading cell centres";
+                st = fail(h, GFM_ERR_CUDA, "reading cell centres");
                 break;
             }
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) {
-            st = GFM_ERR_CUDA;
-            h->last_error = "synchronising stream";
+            st = fail(h, GFM_ERR_CUDA, "synchronising stream");
             break;
         }
         std::string err;
         if (!gfm::build_host_tables(n, F, ho.data(), hn.data(), hC.empty() ? nullptr : hC.data(), renumber, h->ht,
                                     err)) {
-            st = GFM_ERR_ARG;
-            h->last_error = err;
+            st = fail(h, GFM_ERR_ARG, err);
             break;
         }
-        const size_t np = (size_t)h->ht.n_pad, ns = (size_t)h->ht.n_slots;
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gfm::solver_kernel(gfm::Mode::MIXED, h->ht.max_width, 32), 32, 0);
-        h->max_grid = h->sm_count * (occ > 0 ? occ : 1);
-        cudaError_t e = cudaSuccess;
-#define A(ptr, cnt) \
-    if (e == cudaSuccess) e = dalloc(&h->ptr, (cnt))
-        A(owner, F); A(neighbour, F); A(Sf, 3 * (size_t)F); A(C, 3 * (size_t)n);
-        A(perm, n); A(iperm, np); A(slice_ptr, (size_t)h->ht.n_slices + 1); A(col, ns); A(face, ns);
-        A(val64, ns); A(val32, ns);
-        A(lambda, F); A(gamma, F); A(jump, F); A(sigma, F); A(phi, F); A(dl_dlam, F); A(kind, F);
-        A(alpha, n); A(b, np); A(diag, np); A(dinv, np); A(x64, np); A(r64, np); A(p64, np); A(q64, np);
-        A(rhs, np); A(tmp_user, n); A(tmp_user2, n); A(UP0, np); A(UP1, np); A(R32, np); A(S32, np); A(E, np);
-        A(dinv32, np);
-        A(stage_alpha, n); A(stage_phi, F); A(stage_p, n);
-        A(prm, 1); A(bar, 1); A(err, 1); A(partials, 2 * (size_t)h->max_grid * 4); A(dinfo, 1);
-#undef A
-        if (e != cudaSuccess) {
-            st = (e == cudaErrorMemoryAllocation) ? GFM_ERR_NOMEM : GFM_ERR_CUDA;
-            h->last_error = std::string("device allocation: ") + cudaGetErrorString(e);
-            break;
-        }
-        if (cudaMallocHost((void **)&h->hinfo, sizeof(gfm_solve_info)) != cudaSuccess) {
-            st = GFM_ERR_NOMEM;
-            h->last_error = "pinned host allocation";
-            break;
-        }
-        for (auto &ev : h->ev) cudaEventCreate(&ev);
-        // iperm padded with the padding cells' own index
-        std::vector<int32_t> ip(h->ht.iperm);
-        ip.resize(np);
-        for (size_t i = (size_t)n; i < np; ++i) ip[i] = (int32_t)i;
-        e = cudaMemcpyAsync(h->owner, mesh->owner, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, s);
+        h->ht.iperm.resize((size_t)h->ht.n_pad, -1);  // padding cells
+        st = alloc_upload(h, s);
+        if (st != GFM_OK) break;
+        cudaError_t e = cudaMemcpyAsync(h->owner, mesh->owner, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->neighbour, mesh->neighbour, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->Sf, mesh->Sf, sizeof(double) * 3 * F, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->C, mesh->C, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->perm, h->ht.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->iperm, ip.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->slice_ptr, h->ht.slice_ptr.data(), sizeof(int32_t) * (h->ht.n_slices + 1), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->col, h->ht.col.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->face, h->ht.face.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s);
-        // zero every vector once so padding lanes hold finite values
-        double *zero_d[] = {h->b, h->diag, h->dinv, h->x64, h->r64, h->p64, h->q64, h->rhs};
-        for (double *zp : zero_d)
-            if (e == cudaSuccess) e = cudaMemsetAsync(zp, 0, sizeof(double) * np, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->UP0, 0, sizeof(float2) * np, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->UP1, 0, sizeof(float2) * np, s);
-        float *zero_f[] = {h->R32, h->S32, h->E, h->dinv32};
-        for (float *zp : zero_f)
-            if (e == cudaSuccess) e = cudaMemsetAsync(zp, 0, sizeof(float) * np, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            st = GFM_ERR_CUDA;
-            h->last_error = std::string("uploading tables: ") + cudaGetErrorString(e);
-            break;
-        }
+        if (e != cudaSuccess) st = cuda_fail(h, e, "copying the mesh");
     } while (0);
     if (st != GFM_OK) {
         fprintf(stderr, "gfm_create: %s\n", h->last_error.c_str());
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return GFM_OK;
+}
+
+gfm_status gfm_create_batched(const gfm_mesh *meshes, int32_t n_tanks, int32_t renumber, gfm_stream stream,
+                              gfm_handle *out)
+{
+    if (!out) return GFM_ERR_ARG;
+    *out = nullptr;
+    if (!meshes || n_tanks <= 0 || n_tanks > gfm::kMaxTanks || renumber < 0 || renumber > 2) return GFM_ERR_ARG;
+    for (int t = 0; t < n_tanks; ++t) {
+        const gfm_mesh &m = meshes[t];
+        if (!m.owner || !m.neighbour || !m.Sf || !m.C || m.n_cells <= 0 || m.n_faces <= 0) return GFM_ERR_ARG;
+    }
+    gfm_ctx *h = new (std::nothrow) gfm_ctx();
+    if (!h) return GFM_ERR_NOMEM;
+    clear_stale_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    gfm_status st = init_device(h);
+    do {
+        if (st != GFM_OK) break;
+        std::vector<std::vector<int32_t>> ho((size_t)n_tanks), hn((size_t)n_tanks);
+        std::vector<std::vector<double>> hC((size_t)n_tanks);
+        long long ncell = 0, nface = 0;
+        for (int t = 0; t < n_tanks; ++t) {
+            const gfm_mesh &m = meshes[t];
+            ho[(size_t)t].resize((size_t)m.n_faces);
+            hn[(size_t)t].resize((size_t)m.n_faces);
+            cudaError_t e = cudaMemcpyAsync(ho[(size_t)t].data(), m.owner, sizeof(int32_t) * m.n_faces,
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hn[(size_t)t].data(), m.neighbour, sizeof(int32_t) * m.n_faces,
+                                    cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && renumber == 2) {
+                hC[(size_t)t].resize((size_t)3 * m.n_cells);
+                e = cudaMemcpyAsync(hC[(size_t)t].data(), m.C, sizeof(double) * 3 * m.n_cells, cudaMemcpyDeviceToHost,
+                                    s);
+            }
+            if (e != cudaSuccess) {
+                st = cuda_fail(h, e, "reading tank meshes (must be device pointers)");
+                break;
+            }
+            ncell += m.n_cells;
+            nface += m.n_faces;
+        }
+        if (st != GFM_OK) break;
+        if (ncell > INT32_MAX || nface > INT32_MAX) {
+            st = fail(h, GFM_ERR_ARG, "batch too large");
+            break;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            st = fail(h, GFM_ERR_CUDA, "synchronising stream");
+            break;
+        }
+        std::vector<gfm::TankMesh> tm((size_t)n_tanks);
+        for (int t = 0; t < n_tanks; ++t)
+            tm[(size_t)t] = gfm::TankMesh{meshes[t].n_cells, meshes[t].n_faces, ho[(size_t)t].data(),
+                                          hn[(size_t)t].data(), hC[(size_t)t].empty() ? nullptr : hC[(size_t)t].data()};
+        std::string err;
+        if (!gfm::build_batch_tables(tm, renumber, h->ht, h->bt, err)) {
+            st = fail(h, GFM_ERR_ARG, err);
+            break;
+        }
+        h->n = (int)ncell;
+        h->F = (int)nface;
+        h->batched = true;
+        h->T = n_tanks;
+        h->coarse_max = 0;  // the coarse space is per mesh; batched tanks run Jacobi
+        st = alloc_upload(h, s);
+        if (st != GFM_OK) break;
+        st = alloc_batch(h, s);
+        if (st != GFM_OK) break;
+        // caller-order concatenated mesh: indices offset by the tanks' cell offsets
+        std::vector<int32_t> co((size_t)h->F), cn((size_t)h->F);
+        for (int t = 0; t < n_tanks; ++t) {
+            const int32_t c0 = h->bt.coff[(size_t)t], f0 = h->bt.foff[(size_t)t];
+            for (int f = 0; f < meshes[t].n_faces; ++f) {
+                co[(size_t)f0 + f] = ho[(size_t)t][(size_t)f] + c0;
+                cn[(size_t)f0 + f] = hn[(size_t)t][(size_t)f] + c0;
+            }
+        }
+        cudaError_t e = cudaMemcpyAsync(h->owner, co.data(), sizeof(int32_t) * h->F, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->neighbour, cn.data(), sizeof(int32_t) * h->F, cudaMemcpyHostToDevice, s);
+        for (int t = 0; t < n_tanks && e == cudaSuccess; ++t) {
+            const int nt = meshes[t].n_cells, ft = meshes[t].n_faces;
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(h->Sf + (size_t)k * h->F + h->bt.foff[(size_t)t], meshes[t].Sf + (size_t)k * ft,
+                                    sizeof(double) * ft, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h->C + (size_t)k * h->n + h->bt.coff[(size_t)t], meshes[t].C + (size_t)k * nt,
+                                        sizeof(double) * nt, cudaMemcpyDeviceToDevice, s);
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(h, e, "copying the tank meshes");
+            break;
+        }
+        st = plan_batch(h);
+    } while (0);
+    if (st != GFM_OK) {
+        fprintf(stderr, "gfm_create_batched: %s\n", h->last_error.c_str());
         free_all(h);
         delete h;
         return st;
@@ -389,21 +673,41 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
                         gfm_stream stream)
 {
     if (!h) return GFM_ERR_ARG;
+    clear_stale_error();
     if (!alpha || !phi || !phys) return fail(h, GFM_ERR_ARG, "alpha, phi and phys must be non-NULL");
-    if (!(phys->rho_a > 0.0) || !(phys->rho_w >= phys->rho_a) || !std::isfinite(phys->rho_w))
-        return fail(h, GFM_ERR_ARG, "densities must satisfy 0 < rho_a <= rho_w");
-    if (phys->ref_cell < -1 || phys->ref_cell >= h->n) return fail(h, GFM_ERR_ARG, "ref_cell out of range");
-    for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(phys->g[k])) return fail(h, GFM_ERR_ARG, "g must be finite");
+    const int nphys = h->batched ? h->T : 1;
+    for (int t = 0; t < nphys; ++t) {
+        const gfm_phys &ph = phys[t];
+        const int ncell_t = h->batched ? h->bt.ncell[(size_t)t] : h->n;
+        if (!(ph.rho_a > 0.0) || !(ph.rho_w >= ph.rho_a) || !std::isfinite(ph.rho_w))
+            return fail(h, GFM_ERR_ARG, "densities must satisfy 0 < rho_a <= rho_w");
+        if (ph.ref_cell < -1 || ph.ref_cell >= ncell_t) return fail(h, GFM_ERR_ARG, "ref_cell out of range");
+        if (h->batched && ph.ref_cell < 0) return fail(h, GFM_ERR_ARG, "every tank of a batch needs a pinned cell");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(ph.g[k])) return fail(h, GFM_ERR_ARG, "g must be finite");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     h->prof.launches = 0;
     prof_record(h, 4, s);
     prof_record(h, 0, s);
     h->phys = *phys;
-    h->ref_internal = phys->ref_cell >= 0 ? h->ht.perm[(size_t)phys->ref_cell] : -1;
+    h->ref_internal = (h->batched || phys->ref_cell >= 0) ? (h->batched ? 0 : h->ht.perm[(size_t)phys->ref_cell]) : -1;
     GFM_CUDA(h, cudaMemcpyAsync(h->alpha, alpha, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
     GFM_CUDA(h, cudaMemcpyAsync(h->phi, phi, sizeof(double) * h->F, cudaMemcpyDeviceToDevice, s));
     GFM_CUDA(h, cudaMemsetAsync(h->prm, 0, sizeof(gfm::DevParams), s));
+    if (h->batched) {
+        for (int t = 0; t < h->T; ++t) {
+            const gfm_phys &ph = phys[t];
+            gfm::TankPhys tp{ph.rho_w, ph.rho_a, ph.g[0], ph.g[1], ph.g[2], ph.ref_value,
+                             h->ht.perm[(size_t)h->bt.coff[(size_t)t] + ph.ref_cell], 0};
+            h->tphys_h[t] = tp;
+            gfm::DevParams dp{};
+            dp.ref = tp.ref;
+            h->tprm_h[t] = dp;
+        }
+        GFM_CUDA(h, cudaMemcpyAsync(h->tphys, h->tphys_h, sizeof(gfm::TankPhys) * h->T, cudaMemcpyHostToDevice, s));
+        GFM_CUDA(h, cudaMemcpyAsync(h->tprm, h->tprm_h, sizeof(gfm::DevParams) * h->T, cudaMemcpyHostToDevice, s));
+    }
     gfm::FaceArgs fa;
     fa.n = h->n;
     fa.F = h->F;
@@ -423,6 +727,8 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     fa.jump = h->jump;
     fa.sigma = h->sigma;
     fa.kind = h->kind;
+    fa.ftank = h->batched ? h->ftank : nullptr;
+    fa.tphys = h->batched ? h->tphys : nullptr;
     GFM_CUDA(h, gfm::launch_faces(fa, s));
     gfm::CellArgs ca;
     ca.m = sell_of(h);
@@ -435,8 +741,36 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     ca.dinv = h->dinv;
     ca.dinv32 = h->dinv32;
     ca.prm = h->prm;
+    ca.iperm = h->iperm;
+    ca.stank = h->batched ? h->stank : nullptr;
+    ca.tphys = h->batched ? h->tphys : nullptr;
+    ca.tprm = h->batched ? h->tprm : nullptr;
     GFM_CUDA(h, gfm::launch_cells(ca, s));
     int launched = 2;
+    if (!h->batched) {
+        gfm::CoarseArgs co;
+        co.n = h->n;
+        co.F = h->F;
+        co.n_pad = h->ht.n_pad;
+        co.owner = h->owner;
+        co.neighbour = h->neighbour;
+        co.perm = h->perm;
+        co.kind = h->kind;
+        co.gamma = h->gamma;
+        co.ref = h->ref_internal;
+        co.max_k = h->coarse_max;
+        co.min_size = h->coarse_min_size;
+        co.max_cross = h->max_cross;
+        co.prm = h->prm;
+        co.parent = h->cc_parent;
+        co.csize = h->cc_size;
+        co.cand = h->cc_cand;
+        co.counters = h->cc_counters;
+        co.comp = h->comp;
+        co.cross = h->cross;
+        co.coarse = h->coarse;
+        GFM_CUDA(h, gfm::launch_coarse(co, s, &launched));
+    }
     if (h->ref_internal < 0) {  // only an unpinned system needs sum(b) for its compatibility test
         GFM_CUDA(h, gfm::launch_bsums(h->b, h->n, h->prm, s));
         ++launched;
@@ -475,14 +809,17 @@ gfm_status gfm_solve(gfm_handle h, const gfm_solve_opts *opts, double *p, double
     if (!p) return fail(h, GFM_ERR_ARG, "p must be non-NULL");
     if (opts->info_on_device && !info) return fail(h, GFM_ERR_ARG, "info_on_device needs a device info pointer");
     if (!h->assembled) return fail(h, GFM_ERR_STATE, "solve before assemble");
+    clear_stale_error();
     cudaStream_t s = (cudaStream_t)stream;
     if (!opts->info_on_device) {
         st = check_compat(h, s);
         if (st != GFM_OK) return st;
     }
     h->prof.launches = 0;
+    if (h->batched && opts->mode != GFM_MIXED)
+        return fail(h, GFM_ERR_ARG, "a batched handle solves in GFM_MIXED mode");
     prof_record(h, 4, s);
-    gfm_solve_info *idev = opts->info_on_device ? info : h->dinfo;
+    gfm_solve_info *idev = opts->info_on_device ? info : (h->batched ? h->binfos : h->dinfo);
     st = enqueue_solve(h, opts, h->b, p, opts->use_x0, idev, s);
     if (st != GFM_OK) return st;
     if (phi_corr) {
@@ -504,6 +841,8 @@ gfm_status gfm_solve_adjoint(gfm_handle h, const gfm_solve_opts *opts, const dou
     if (!p || !dL_dp || !dL_dphi || !dL_dalpha) return fail(h, GFM_ERR_ARG, "p, dL_dp, dL_dphi, dL_dalpha required");
     if (opts->info_on_device && !info) return fail(h, GFM_ERR_ARG, "info_on_device needs a device info pointer");
     if (!h->assembled) return fail(h, GFM_ERR_STATE, "adjoint before assemble");
+    if (h->batched) return fail(h, GFM_ERR_ARG, "the adjoint solve takes a single-mesh handle");
+    clear_stale_error();
     cudaStream_t s = (cudaStream_t)stream;
     h->prof.launches = 0;
     prof_record(h, 4, s);
@@ -553,6 +892,8 @@ gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *
     gfm_status st = check_opts(h, opts);
     if (st != GFM_OK) return st;
     if (opts->info_on_device) return fail(h, GFM_ERR_ARG, "gfm_solve_host reports info on the host");
+    if (h->batched) return fail(h, GFM_ERR_ARG, "gfm_solve_host takes a single-mesh handle");
+    clear_stale_error();
     cudaStream_t s = (cudaStream_t)stream;
     GFM_CUDA(h, cudaMemcpyAsync(h->stage_alpha, alpha_host, sizeof(double) * h->n, cudaMemcpyHostToDevice, s));
     GFM_CUDA(h, cudaMemcpyAsync(h->stage_phi, phi_host, sizeof(double) * h->F, cudaMemcpyHostToDevice, s));
@@ -577,13 +918,25 @@ gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t)
     if (t->ctas_per_sm) nt.ctas_per_sm = t->ctas_per_sm;
     if (nt.threads < 32 || nt.threads > gfm::solver_max_threads() || nt.threads % 32 || nt.ctas_per_sm < 1)
         return fail(h, GFM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024], ctas_per_sm >= 1");
+    if (h->sm_count * nt.ctas_per_sm > h->max_grid) return fail(h, GFM_ERR_ARG, "grid larger than workspace");
+    const gfm_tuning old = h->tuning;
+    h->tuning = nt;
+    if (h->batched && plan_batch(h) != GFM_OK) {
+        h->tuning = old;
+        plan_batch(h);
+        return fail(h, GFM_ERR_ARG, "launch shape has fewer CTAs than tanks");
+    }
     for (gfm::Mode m : {gfm::Mode::FP64, gfm::Mode::MIXED}) {
         int occ = 0;
-        GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gfm::solver_kernel(m, h->ht.max_width, nt.threads), nt.threads, 0));
-        if (occ < nt.ctas_per_sm) return fail(h, GFM_ERR_ARG, "launch shape cannot be co-resident");
+        const void *k = gfm::solver_kernel(m, h->ht.max_width, nt.threads);
+        GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nt.threads, 0));
+        LaunchPlan lp;
+        if (occ < nt.ctas_per_sm || plan_launch(h, m, &lp) != GFM_OK) {
+            h->tuning = old;
+            plan_batch(h);
+            return fail(h, GFM_ERR_ARG, "launch shape cannot be co-resident");
+        }
     }
-    if (h->sm_count * nt.ctas_per_sm > h->max_grid) return fail(h, GFM_ERR_ARG, "grid larger than workspace");
-    h->tuning = nt;
     return GFM_OK;
 }
 
@@ -591,6 +944,30 @@ gfm_status gfm_get_tuning(gfm_handle h, gfm_tuning *t)
 {
     if (!h || !t) return GFM_ERR_ARG;
     *t = h->tuning;
+    return GFM_OK;
+}
+
+gfm_status gfm_set_coarse(gfm_handle h, int32_t max_vectors, int32_t min_size)
+{
+    if (!h) return GFM_ERR_ARG;
+    if (max_vectors < 0 || max_vectors > gfm::kMaxCoarse || min_size < 1)
+        return fail(h, GFM_ERR_ARG, "max_vectors must be in [0, 8] and min_size >= 1");
+    h->coarse_max = max_vectors;
+    h->coarse_min_size = min_size;
+    return GFM_OK;
+}
+
+gfm_status gfm_get_coarse(gfm_handle h, int32_t *n_vectors, int32_t *n_regions, int32_t *sizes, gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    gfm::Coarse co;
+    cudaStream_t s = (cudaStream_t)stream;
+    GFM_CUDA(h, cudaMemcpyAsync(&co, h->coarse, sizeof co, cudaMemcpyDeviceToHost, s));
+    GFM_CUDA(h, cudaStreamSynchronize(s));
+    if (n_vectors) *n_vectors = co.K;
+    if (n_regions) *n_regions = co.n_cand;
+    if (sizes)
+        for (int k = 0; k < gfm::kMaxCoarse; ++k) sizes[k] = k < co.K ? co.sizes[k] : 0;
     return GFM_OK;
 }
 
@@ -605,10 +982,12 @@ gfm_status gfm_get_profile(gfm_handle h, gfm_profile *out)
 {
     if (!h || !out) return GFM_ERR_ARG;
     if (h->profiling) {
-        cudaEventSynchronize(h->ev[5]);
-        cudaEventElapsedTime(&h->prof.ms_assemble, h->ev[0], h->ev[1]);
-        cudaEventElapsedTime(&h->prof.ms_solve, h->ev[2], h->ev[3]);
-        cudaEventElapsedTime(&h->prof.ms_total, h->ev[4], h->ev[5]);
+        for (int k = 0; k < 6; ++k)
+            if (h->ev_recorded[k]) cudaEventSynchronize(h->ev[k]);
+        h->prof.ms_assemble = prof_elapsed(h, 0, 1);
+        h->prof.ms_solve = prof_elapsed(h, 2, 3);
+        h->prof.ms_total = prof_elapsed(h, 4, 5);
+        (void)cudaGetLastError();
     }
     *out = h->prof;
     return GFM_OK;
@@ -619,7 +998,7 @@ gfm_status gfm_get_sizes(gfm_handle h, int32_t *n_cells, int32_t *n_faces, int32
     if (!h) return GFM_ERR_ARG;
     if (n_cells) *n_cells = h->n;
     if (n_faces) *n_faces = h->F;
-    if (n_tanks) *n_tanks = 1;
+    if (n_tanks) *n_tanks = h->batched ? h->T : 1;
     return GFM_OK;
 }
 

@@ -44,19 +44,28 @@ __global__ void k_faces(FaceArgs a)
         const double aW = a.alpha[W], aD = a.alpha[D];
         lam = (aW - 0.5) / (aW - aD);
     }
+    double rho_w = a.rho_w, rho_a = a.rho_a, g0 = a.g0, g1 = a.g1, g2 = a.g2;
+    if (a.ftank) {
+        const TankPhys tp = a.tphys[a.ftank[f]];
+        rho_w = tp.rho_w;
+        rho_a = tp.rho_a;
+        g0 = tp.g0;
+        g1 = tp.g1;
+        g2 = tp.g2;
+    }
     const double Sx = a.Sf[f], Sy = a.Sf[F + f], Sz = a.Sf[2 * F + f];
     const double dx = a.C[nb] - a.C[o];
     const double dy = a.C[n + nb] - a.C[n + o];
     const double dz = a.C[2 * n + nb] - a.C[2 * n + o];
     const double c = (Sx * Sx + Sy * Sy + Sz * Sz) / (Sx * dx + Sy * dy + Sz * dz);
-    const double rf = lam * a.rho_w + (1.0 - lam) * a.rho_a;
+    const double rf = lam * rho_w + (1.0 - lam) * rho_a;
     const double gam = c / rf;
     double J = 0.0;
     if (kind >= kIfOwnerWet) {
         const double xg0 = a.C[W] + lam * (a.C[D] - a.C[W]);
         const double xg1 = a.C[n + W] + lam * (a.C[n + D] - a.C[n + W]);
         const double xg2 = a.C[2 * n + W] + lam * (a.C[2 * n + D] - a.C[2 * n + W]);
-        const double H = (a.rho_w - a.rho_a) * ((a.g0 * xg0 + a.g1 * xg1) + a.g2 * xg2);
+        const double H = (rho_w - rho_a) * ((g0 * xg0 + g1 * xg1) + g2 * xg2);
         J = (kind == kIfOwnerWet) ? H : -H;
     }
     a.lambda[f] = lam;
@@ -74,9 +83,19 @@ __global__ void k_faces(FaceArgs a)
 __global__ void k_cells(CellArgs a)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) a.prm->ref = a.ref;
+    if (t == 0 && !a.stank) a.prm->ref = a.ref;
     if (t >= a.m.n_pad) return;
     const int s = t >> 5, l = t & 31;
+    int ref = a.ref;
+    double ref_value = a.ref_value;
+    DevParams *prm = a.prm;
+    if (a.stank) {
+        const int tk = a.stank[s];
+        ref = a.tphys[tk].ref;
+        ref_value = a.tphys[tk].ref_value;
+        prm = a.tprm + tk;
+    }
+    const bool valid = a.iperm[t] >= 0;
     const int base = a.m.slice_ptr[s];
     const int w = (a.m.slice_ptr[s + 1] - base) >> 5;
     double diag = 0.0, b = 0.0;
@@ -96,16 +115,16 @@ __global__ void k_cells(CellArgs a)
         a.m.val64[slot] = g;
         a.m.val32[slot] = (float)g;
     }
-    if (t == a.ref) {
-        b = b + diag * a.ref_value;
-        a.prm->pin64 = diag;
-        a.prm->pin32 = (float)diag;
+    if (t == ref) {
+        b = b + diag * ref_value;
+        prm->pin64 = diag;
+        prm->pin32 = (float)diag;
         diag = diag + diag;
     }
-    a.b[t] = (t < a.m.n) ? b : 0.0;
-    a.diag[t] = (t < a.m.n) ? diag : 0.0;
-    a.dinv[t] = (t < a.m.n) ? 1.0 / diag : 0.0;
-    a.dinv32[t] = (t < a.m.n) ? 1.0f / (float)diag : 0.0f;
+    a.b[t] = valid ? b : 0.0;
+    a.diag[t] = valid ? diag : 0.0;
+    a.dinv[t] = valid ? 1.0 / diag : 0.0;
+    a.dinv32[t] = valid ? 1.0f / (float)diag : 0.0f;
 }
 
 // sum(b) and sum(|b|) by one block, fixed order (compatibility check of an
@@ -209,13 +228,15 @@ __global__ void k_adjoint_cells(AdjointArgs a)
     a.dL_dalpha[me] = acc;
 }
 
-// dst[i] = src[iperm[i]] (caller order -> internal order), zero padding.
+// dst[i] = src[iperm[i]] (caller order -> internal order), zero on padding
+// cells (iperm = -1).
 __global__ void k_gather(const double *__restrict__ src, const int32_t *__restrict__ iperm, double *__restrict__ dst,
                          int n, int n_pad)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
-    dst[i] = (i < n) ? src[iperm[i]] : 0.0;
+    const int c = iperm[i];
+    dst[i] = (c >= 0) ? src[c] : 0.0;
 }
 
 static inline int blocks_for(long long work, int threads) { return (int)((work + threads - 1) / threads); }

@@ -1,0 +1,241 @@
+// Coarse space of the two-level preconditioner, rebuilt by every assembly.
+//
+// With a density ratio of 1000 the ghost-fluid Laplacian (Sec. 3.1) couples
+// a region of one phase to the rest only through its interface faces, whose
+// coefficients are of the order of the heavy phase's, so the Jacobi-scaled
+// operator has a few near-null vectors: roughly constant on each large
+// connected region of one phase.  Jacobi-PCG spends thousands of iterations
+// on a plateau resolving them.  The preconditioner adds the Galerkin
+// correction Z (Z^T A Z)^{-1} Z^T on the span Z of those regions' indicator
+// vectors; this file finds the regions and forms E = Z^T A Z.
+//
+// Regions: union-find over the non-interface faces (same phase on both
+// sides), linking the larger root under the smaller, so each region's root
+// is its smallest cell index whatever the order of the atomic operations.
+// The up-to-kMaxCoarse largest regions of at least min_size cells are kept.
+#include "gfm_internal.h"
+
+namespace gfm {
+
+namespace {
+
+__device__ __forceinline__ int cc_find(int *parent, int x)
+{
+    volatile int *P = parent;
+    for (;;) {
+        const int p = P[x];
+        if (p == x) return x;
+        const int gp = P[p];
+        if (gp != p) P[x] = gp;  // path splitting: gp is an ancestor of x
+        x = p;
+    }
+}
+
+__device__ __forceinline__ void cc_union(int *parent, int a, int b)
+{
+    for (;;) {
+        a = cc_find(parent, a);
+        b = cc_find(parent, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(parent + a, a, b) == a) return;
+    }
+}
+
+__global__ void k_cc_init(int n, int *parent, int *csize)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    parent[i] = i;
+    csize[i] = 0;
+}
+
+// Faces with both cells of the same phase (kind 0: both dry, 1: both wet).
+__global__ void k_cc_hook(int F, const int32_t *__restrict__ owner, const int32_t *__restrict__ nb,
+                          const int8_t *__restrict__ kind, int *parent)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F || kind[f] > 1) return;
+    cc_union(parent, owner[f], nb[f]);
+}
+
+__global__ void k_cc_count(int n, int *parent, int *csize)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = cc_find(parent, i);
+    parent[i] = r;
+    atomicAdd(csize + r, 1);
+}
+
+__global__ void k_cc_candidates(int n, const int *__restrict__ parent, const int *__restrict__ csize, int min_size,
+                                int *cand, int *counters)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || parent[i] != i || csize[i] < min_size) return;
+    const int k = atomicAdd(counters, 1);
+    if (k < kMaxCandidates) cand[k] = i;
+}
+
+// One warp: pick the up-to-max_k largest regions (ties: smaller root first).
+__global__ void k_cc_select(const int *__restrict__ csize, const int *__restrict__ cand, int *counters, int max_k,
+                            int ref, Coarse *co)
+{
+    const int lane = threadIdx.x;
+    const int nc = min(counters[0], kMaxCandidates);
+    int K = 0;
+    int chosen[kMaxCoarse];
+    if (ref >= 0) {
+        for (int k = 0; k < max_k && k < kMaxCoarse; ++k) {
+            long long best = -1;  // key = size * 2^32 + (2^31 - 1 - root)
+            for (int t = lane; t < nc; t += 32) {
+                const int c = cand[t];
+                bool taken = false;
+                for (int q = 0; q < K; ++q) taken |= (chosen[q] == c);
+                if (taken) continue;
+                const long long key = ((long long)csize[c] << 32) | (long long)(0x7fffffff - c);
+                if (key > best) best = key;
+            }
+            for (int off = 16; off; off >>= 1) {
+                const long long o = __shfl_xor_sync(0xffffffffu, best, off);
+                if (o > best) best = o;
+            }
+            if (best < 0) break;
+            chosen[K++] = 0x7fffffff - (int)(best & 0xffffffffLL);
+        }
+    }
+    if (lane == 0) {
+        co->K = K;
+        co->n_cand = counters[0];
+        co->n_cross = 0;
+        co->ref_comp = -1;
+        for (int k = 0; k < kMaxCoarse; ++k) {
+            co->roots[k] = k < K ? chosen[k] : -1;
+            co->sizes[k] = k < K ? csize[chosen[k]] : 0;
+        }
+        for (int q = 0; q < kMaxCoarse * kMaxCoarse; ++q) {
+            co->E[q] = 0.0;
+            co->Einv[q] = 0.0;
+        }
+        counters[1] = 0;
+    }
+}
+
+__global__ void k_cc_label(int n, const int *__restrict__ parent, const int32_t *__restrict__ perm,
+                           const Coarse *__restrict__ co, int8_t *comp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = parent[i];
+    int id = -1;
+    for (int k = 0; k < co->K; ++k)
+        if (co->roots[k] == r) id = k;
+    comp[perm[i]] = (int8_t)id;
+}
+
+// Faces joining different coarse regions: listed, and summed into
+// E = Z^T A Z (A = sum_f gamma_f (e_o - e_v)(e_o - e_v)^T + pin).
+__global__ void k_coarse_faces(int F, const int32_t *__restrict__ owner, const int32_t *__restrict__ nb,
+                               const int32_t *__restrict__ perm, const int8_t *__restrict__ comp,
+                               const double *__restrict__ gamma, Coarse *co, CrossFace *cross, int *counters,
+                               int max_cross)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F || co->K == 0) return;
+    const int o = perm[owner[f]], v = perm[nb[f]];
+    const int a = comp[o], b = comp[v];
+    if (a == b) return;
+    const double g = gamma[f];
+    const int k = atomicAdd(counters + 1, 1);
+    if (k < max_cross) {
+        CrossFace c;
+        c.o = o;
+        c.v = v;
+        c.a = (int8_t)a;
+        c.b = (int8_t)b;
+        c.g32 = (float)g;
+        c.g64 = g;
+        cross[k] = c;
+    }
+    if (a >= 0) atomicAdd(&co->E[a * kMaxCoarse + a], g);
+    if (b >= 0) atomicAdd(&co->E[b * kMaxCoarse + b], g);
+    if (a >= 0 && b >= 0) {
+        atomicAdd(&co->E[a * kMaxCoarse + b], -g);
+        atomicAdd(&co->E[b * kMaxCoarse + a], -g);
+    }
+}
+
+// Pin term, Cholesky inverse of E (K <= 8, one thread); K = 0 when anything
+// is off (cross-face list overflow, E not positive definite).
+__global__ void k_coarse_finish(const int8_t *__restrict__ comp, int ref, const DevParams *__restrict__ prm,
+                                Coarse *co, const int *counters, int max_cross)
+{
+    int K = co->K;
+    const int nx = counters[1];
+    if (K > 0 && nx > max_cross) K = 0;
+    co->n_cross = nx < max_cross ? nx : max_cross;
+    co->ref_comp = (ref >= 0 && K > 0) ? comp[ref] : -1;
+    if (co->ref_comp >= 0) co->E[co->ref_comp * kMaxCoarse + co->ref_comp] += prm->pin64;
+    double L[kMaxCoarse][kMaxCoarse];
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) L[i][j] = 0.0;
+    for (int j = 0; j < K && K > 0; ++j) {
+        double d = co->E[j * kMaxCoarse + j];
+        for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
+        if (!(d > 0.0)) {
+            K = 0;
+            break;
+        }
+        d = sqrt(d);
+        L[j][j] = d;
+        for (int i = j + 1; i < K; ++i) {
+            double t = co->E[i * kMaxCoarse + j];
+            for (int q = 0; q < j; ++q) t -= L[i][q] * L[j][q];
+            L[i][j] = t / d;
+        }
+    }
+    // columns of E^{-1}: solve L L^T x = e_c
+    for (int c = 0; c < K; ++c) {
+        double y[kMaxCoarse];
+        for (int i = 0; i < K; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int q = 0; q < i; ++q) t -= L[i][q] * y[q];
+            y[i] = t / L[i][i];
+        }
+        for (int i = K - 1; i >= 0; --i) {
+            double t = y[i];
+            for (int q = i + 1; q < K; ++q) t -= L[q][i] * y[q];
+            y[i] = t / L[i][i];
+        }
+        for (int i = 0; i < K; ++i) co->Einv[i * kMaxCoarse + c] = y[i];
+    }
+    co->K = K;
+}
+
+inline int blocks_for(long long work, int threads) { return (int)((work + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches)
+{
+    const int T = 256;
+    cudaError_t e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_cc_init<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.csize);
+    k_cc_hook<<<blocks_for(a.F, T), T, 0, s>>>(a.F, a.owner, a.neighbour, a.kind, a.parent);
+    k_cc_count<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.csize);
+    k_cc_candidates<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.csize, a.min_size, a.cand, a.counters);
+    k_cc_select<<<1, 32, 0, s>>>(a.csize, a.cand, a.counters, a.max_k, a.ref, a.coarse);
+    k_cc_label<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.perm, a.coarse, a.comp);
+    k_coarse_faces<<<blocks_for(a.F, T), T, 0, s>>>(a.F, a.owner, a.neighbour, a.perm, a.comp, a.gamma, a.coarse,
+                                                    a.cross, a.counters, a.max_cross);
+    k_coarse_finish<<<1, 1, 0, s>>>(a.comp, a.ref, a.prm, a.coarse, a.counters, a.max_cross);
+    if (launches) *launches += 8;
+    return cudaGetLastError();
+}
+
+}  // namespace gfm

@@ -10,6 +10,41 @@
 namespace gfm {
 
 constexpr int kSlice = 32;  // cells per sliced-ELL slice (one warp, one lane per cell)
+constexpr int kMaxCoarse = 8;         // coarse vectors of the two-level preconditioner
+constexpr int kMaxCandidates = 4096;  // components examined when choosing them
+constexpr int kMaxTanks = 128;        // tanks of one batched solve
+
+// Physics of one tank of a batch (device copy of gfm_phys, ref internal).
+struct TankPhys {
+    double rho_w, rho_a, g0, g1, g2, ref_value;
+    int32_t ref;  // internal index of the pinned cell, -1 = none
+    int32_t pad;
+};
+
+// Two-level preconditioner data, rebuilt by every assembly.  The coarse space
+// is spanned by the indicator vectors of the largest connected regions of one
+// phase (cells joined by non-interface faces); E = Z^T A Z and its inverse.
+// Faces whose two cells lie in different coarse regions (or one in none) are
+// listed so that Z^T (A v) can be formed from them exactly.
+struct Coarse {
+    int32_t K;       // coarse vectors in use (0 = Jacobi only)
+    int32_t n_cand;  // regions of at least min_size cells
+    int32_t n_cross; // listed cross faces
+    int32_t ref_comp;  // coarse region of the pinned cell, -1 = none
+    int32_t roots[kMaxCoarse];
+    int32_t sizes[kMaxCoarse];
+    double E[kMaxCoarse * kMaxCoarse];
+    double Einv[kMaxCoarse * kMaxCoarse];
+};
+
+// One face between two coarse regions: internal cell indices, coefficient,
+// and the regions (a of cell o, b of cell v; -1 = not in a coarse region).
+struct CrossFace {
+    int32_t o, v;
+    int8_t a, b;
+    float g32;
+    double g64;
+};
 
 // Written on the device by the assembly, read by the solver kernels, so that
 // assembling and solving need no host round trip.
@@ -56,6 +91,12 @@ struct SolveArgs {
     double rtol, inner_rtol;
     int32_t max_iters, max_refine, use_x0;
     unsigned long long budget_ns;
+    const Coarse *coarse;  // two-level preconditioner (K = 0: Jacobi only)
+    const int8_t *comp;    // [n_pad] coarse region of each internal cell, -1 none
+    const CrossFace *cross;  // [coarse->n_cross]
+    const int32_t *n_per_tank;  // batched: real cells of each tank (else nullptr)
+    int32_t cache_cap;     // slots of a CTA's slice tables staged in shared memory
+    int32_t meta_slots;    // slice-metadata entries reserved in shared memory
     unsigned int *bar;     // grid-barrier arrival counter (zeroed before launch)
     int *err;              // device status (zeroed before launch)
     double *partials;      // [2][grid][4] per-CTA partial sums
@@ -71,6 +112,8 @@ struct FaceArgs {
     double rho_w, rho_a, g0, g1, g2;
     double *lambda, *gamma, *jump, *sigma;
     int8_t *kind;
+    const int32_t *ftank;    // batched: tank of each face (else nullptr)
+    const TankPhys *tphys;   // batched: physics per tank
 };
 cudaError_t launch_faces(const FaceArgs &a, cudaStream_t s);
 
@@ -82,9 +125,28 @@ struct CellArgs {
     double *b, *diag, *dinv;
     float *dinv32;
     DevParams *prm;
+    const int32_t *iperm;    // internal -> caller (-1 on padding cells)
+    const int32_t *stank;    // batched: tank of each slice (else nullptr)
+    const TankPhys *tphys;   // batched: ref cell and value per tank
+    DevParams *tprm;         // batched: pin per tank
 };
 cudaError_t launch_cells(const CellArgs &a, cudaStream_t s);
 cudaError_t launch_bsums(const double *b, int32_t n, DevParams *prm, cudaStream_t s);
+
+struct CoarseArgs {
+    int32_t n, F, n_pad;
+    const int32_t *owner, *neighbour, *perm;
+    const int8_t *kind;
+    const double *gamma;
+    int32_t ref;  // internal index of the pinned cell, -1 none
+    int32_t max_k, min_size, max_cross;
+    const DevParams *prm;
+    int32_t *parent, *csize, *cand, *counters;  // counters[0] = candidates, [1] = cross faces
+    int8_t *comp;  // internal order
+    CrossFace *cross;
+    Coarse *coarse;
+};
+cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches);
 
 cudaError_t launch_corrected_flux(int32_t F, const int32_t *owner, const int32_t *neighbour, const double *gamma,
                                   const double *jump, const double *phi, const double *p, double *out,
@@ -110,6 +172,18 @@ cudaError_t launch_gather(const double *src_user, const int32_t *iperm, double *
                           int32_t n_pad, cudaStream_t s);
 
 // ---- solver (gfm_solve.cu) ----------------------------------------------
+// Batched solve: every CTA works on one tank (cta[b] = {tank, s0, s1, end},
+// end = internal index one past the tank's last real cell); tank_cta[t] =
+// {first CTA, one past the last}.
+struct BatchArgs {
+    int32_t T;
+    const int4 *cta;
+    const int2 *tank_cta;
+    const DevParams *tprm;
+    gfm_solve_info *infos;  // [T]
+};
+const void *batched_kernel(int max_width);
+
 enum class Mode { FP64 = 0, MIXED = 1 };
 const void *solver_kernel(Mode m, int max_width, int threads);
 int solver_max_threads();

@@ -236,4 +236,115 @@ bool build_host_tables(int n, int F, const int32_t *owner, const int32_t *nb, co
     return true;
 }
 
+bool build_batch_tables(const std::vector<TankMesh> &tanks, int renumber, HostTables &t, BatchTables &bt,
+                        std::string &err)
+{
+    const int T = (int)tanks.size();
+    bt.T = T;
+    bt.coff.assign((size_t)T + 1, 0);
+    bt.foff.assign((size_t)T + 1, 0);
+    bt.ioff.assign((size_t)T + 1, 0);
+    bt.ncell.assign((size_t)T, 0);
+    std::vector<HostTables> per((size_t)T);
+    for (int k = 0; k < T; ++k) {
+        const TankMesh &m = tanks[(size_t)k];
+        if (m.n <= 0 || m.F <= 0) {
+            err = "tank " + std::to_string(k) + ": needs cells and internal faces";
+            return false;
+        }
+        std::string e;
+        if (!build_host_tables(m.n, m.F, m.owner, m.nb, m.C, renumber, per[(size_t)k], e)) {
+            err = "tank " + std::to_string(k) + ": " + e;
+            return false;
+        }
+        bt.coff[(size_t)k + 1] = bt.coff[(size_t)k] + m.n;
+        bt.foff[(size_t)k + 1] = bt.foff[(size_t)k] + m.F;
+        bt.ioff[(size_t)k + 1] = bt.ioff[(size_t)k] + per[(size_t)k].n_pad;
+        bt.ncell[(size_t)k] = m.n;
+    }
+    const long long n = bt.coff[(size_t)T], np = bt.ioff[(size_t)T];
+    if (np > INT32_MAX) {
+        err = "batch too large for 32-bit cell indices";
+        return false;
+    }
+    t.n = (int)n;
+    t.n_pad = (int)np;
+    t.n_slices = (int)(np / kSliceH);
+    t.perm.assign((size_t)n, 0);
+    t.iperm.assign((size_t)np, -1);
+    t.slice_ptr.assign((size_t)t.n_slices + 1, 0);
+    bt.slice_tank.assign((size_t)t.n_slices, 0);
+    bt.face_tank.assign((size_t)bt.foff[(size_t)T], 0);
+    long long slots = 0;
+    for (int k = 0; k < T; ++k) slots += per[(size_t)k].n_slots;
+    if (slots > INT32_MAX) {
+        err = "batch too large for 32-bit slot offsets";
+        return false;
+    }
+    t.n_slots = (int)slots;
+    t.col.assign((size_t)slots, 0);
+    t.face.assign((size_t)slots, 0);
+    t.max_width = 0;
+    int s_at = 0;
+    int32_t slot_at = 0;
+    for (int k = 0; k < T; ++k) {
+        const HostTables &h = per[(size_t)k];
+        const int32_t co = bt.coff[(size_t)k], fo = bt.foff[(size_t)k], io = bt.ioff[(size_t)k];
+        for (int i = 0; i < h.n; ++i) {
+            t.perm[(size_t)co + i] = io + h.perm[(size_t)i];
+            t.iperm[(size_t)io + h.perm[(size_t)i]] = co + i;
+        }
+        for (int f = 0; f < tanks[(size_t)k].F; ++f) bt.face_tank[(size_t)fo + f] = k;
+        for (int sl = 0; sl < h.n_slices; ++sl) {
+            t.slice_ptr[(size_t)s_at + sl + 1] = slot_at + h.slice_ptr[(size_t)sl + 1];
+            bt.slice_tank[(size_t)s_at + sl] = k;
+        }
+        for (int q = 0; q < h.n_slots; ++q) {
+            t.col[(size_t)slot_at + q] = io + h.col[(size_t)q];
+            const int32_t code = h.face[(size_t)q];
+            t.face[(size_t)slot_at + q] = code == 0 ? 0 : (code > 0 ? code + fo : code - fo);
+        }
+        t.max_width = std::max(t.max_width, h.max_width);
+        s_at += h.n_slices;
+        slot_at += h.n_slots;
+    }
+    return true;
+}
+
+bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4, std::vector<int32_t> &tank2,
+                     std::string &err)
+{
+    const int T = bt.T;
+    if (grid < T) {
+        err = "a batched solve needs at least one CTA per tank (" + std::to_string(T) + " tanks, grid " +
+              std::to_string(grid) + ")";
+        return false;
+    }
+    std::vector<long long> sl((size_t)T);
+    for (int k = 0; k < T; ++k) sl[(size_t)k] = (bt.ioff[(size_t)k + 1] - bt.ioff[(size_t)k]) / kSliceH;
+    std::vector<int> g((size_t)T, 1);
+    for (int extra = grid - T; extra > 0; --extra) {
+        int best = 0;
+        for (int k = 1; k < T; ++k)  // load per CTA, compared exactly: sl_k / g_k > sl_b / g_b
+            if (sl[(size_t)k] * g[(size_t)best] > sl[(size_t)best] * g[(size_t)k]) best = k;
+        g[(size_t)best] += 1;
+    }
+    cta4.assign((size_t)grid * 4, 0);
+    tank2.assign((size_t)T * 2, 0);
+    int b = 0;
+    for (int k = 0; k < T; ++k) {
+        const int s_first = bt.ioff[(size_t)k] / kSliceH;
+        const int end = bt.ioff[(size_t)k] + bt.ncell[(size_t)k];
+        tank2[(size_t)k * 2] = b;
+        for (int q = 0; q < g[(size_t)k]; ++q, ++b) {
+            cta4[(size_t)b * 4 + 0] = k;
+            cta4[(size_t)b * 4 + 1] = s_first + (int)((sl[(size_t)k] * q) / g[(size_t)k]);
+            cta4[(size_t)b * 4 + 2] = s_first + (int)((sl[(size_t)k] * (q + 1)) / g[(size_t)k]);
+            cta4[(size_t)b * 4 + 3] = end;
+        }
+        tank2[(size_t)k * 2 + 1] = b;
+    }
+    return true;
+}
+
 }  // namespace gfm

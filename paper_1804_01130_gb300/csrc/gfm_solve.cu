@@ -72,7 +72,7 @@ __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
 
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
 
-constexpr int kMaxNR = 6;
+constexpr int kMaxNR = 12;
 
 // Values decided by thread 0 and broadcast to the CTA.
 struct Ctl {
@@ -86,6 +86,12 @@ struct Shared {
     double warp_d[32][kMaxNR];
     double out[kMaxNR];
     Ctl ctl;
+    double y[kMaxCoarse];    // thread 0: Z^T r (coarse components of the residual)
+    double c64[kMaxCoarse];  // coarse correction E^{-1} Z^T r, broadcast
+    float c32[kMaxCoarse];
+    float zb32[kMaxCoarse];  // this CTA's Z^T (A p) in a pass (shared-memory atomics)
+    double zb64[kMaxCoarse];
+    double Einv[kMaxCoarse * kMaxCoarse];  // staged copy of the coarse inverse
     int flag;
 };
 
@@ -101,7 +107,7 @@ struct Grid {
 
 // Grid-wide barrier.  Returns false if the solve must stop (a timeout here or
 // an error recorded by any CTA).
-__device__ bool grid_sync(Grid &g, Shared &sh)
+__device__ __forceinline__ bool grid_sync(Grid &g, Shared &sh)
 {
     __syncthreads();
     g.epoch += 1u;
@@ -128,20 +134,23 @@ __device__ bool grid_sync(Grid &g, Shared &sh)
     return sh.flag == 0;
 }
 
-// Deterministic all-reduce of NR doubles.  `blk` must hold this CTA's partial
-// sums in thread 0.  Warp k sums value k over all CTAs (lane l takes CTAs
-// l, l+32, ...; then a butterfly), identically in every CTA.
+// Deterministic all-reduce of the first `nr` (<= NR) of NR doubles.  `blk`
+// must hold this CTA's partial sums in thread 0.  Warp w sums values w,
+// w + warps, ... over all CTAs (lane l takes CTAs l, l+32, ...; then a
+// butterfly), identically in every CTA.
 template <int NR>
-__device__ bool grid_allreduce(Grid &g, Shared &sh, const double (&blk)[NR], double (&out)[NR])
+__device__ __forceinline__ bool grid_allreduce(Grid &g, Shared &sh, const double (&blk)[NR], double (&out)[NR],
+                                               int nr = NR)
 {
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) g.partials[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
+        for (int k = 0; k < NR; ++k)
+            if (k < nr) g.partials[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
     }
     if (!grid_sync(g, sh)) return false;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < NR) {
-        const double *src = g.partials + ((size_t)g.parity * kMaxNR + warp) * g.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < nr; k += nw) {
+        const double *src = g.partials + ((size_t)g.parity * kMaxNR + k) * g.G;
         double v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -152,18 +161,18 @@ __device__ bool grid_allreduce(Grid &g, Shared &sh, const double (&blk)[NR], dou
         for (int b = lane + 256; b < g.G; b += 32) acc += __ldcg(src + b);
 #pragma unroll
         for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) sh.out[warp] = acc;
+        if (lane == 0) sh.out[k] = acc;
     }
     g.parity ^= 1;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NR; ++k) out[k] = sh.out[k];
+    for (int k = 0; k < NR; ++k) out[k] = (k < nr) ? sh.out[k] : 0.0;
     return true;
 }
 
 // Block reduction of per-thread FP64 partials into thread 0 (fixed order).
 template <int NR>
-__device__ void block_sum_f64(Shared &sh, double (&v)[NR])
+__device__ __forceinline__ void block_sum_f64(Shared &sh, double (&v)[NR])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -229,7 +238,7 @@ __device__ __forceinline__ FF ff_shfl_tree(FF v)
 // Block reduction of per-thread double-float partials; result (FP64) in
 // thread 0.  Warps and the block both reduce in double-float.
 template <int NR>
-__device__ void block_sum_ff(Shared &sh, FF (&v)[NR], double (&out)[NR])
+__device__ __forceinline__ void block_sum_ff(Shared &sh, FF (&v)[NR], double (&out)[NR])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -275,6 +284,61 @@ __device__ __forceinline__ Row row_of(const Sell &m, int s)
 {
     const int base = __ldg(m.slice_ptr + s);
     return Row{base, (__ldg(m.slice_ptr + s + 1) - base) >> 5};
+}
+
+// A CTA's view of its slices' tables: slice (base, width) for every slice of
+// the CTA and the first `cap` of its slots (neighbour index + coefficient)
+// staged in shared memory at kernel start.  The tables do not change during
+// a solve, so every pass then reads them from shared memory instead of L2.
+template <typename V>
+struct Tab {
+    const int2 *meta;    // [s1 - s0] (global slot base, width)
+    const int32_t *col;  // [cap]
+    const V *val;        // [cap]
+    const int32_t *gcol; // global tables for slots past the cache
+    const V *gval;
+    int s0, base0, end;  // first slice; slot of its first lane; first uncached slot
+
+    __device__ __forceinline__ Row row(int s) const
+    {
+        const int2 m = meta[s - s0];
+        return Row{m.x, m.y};
+    }
+    __device__ __forceinline__ int c(int slot) const { return slot < end ? col[slot - base0] : __ldg(gcol + slot); }
+    __device__ __forceinline__ V v(int slot) const { return slot < end ? val[slot - base0] : __ldg(gval + slot); }
+};
+
+// Stage the CTA's tables; dynamic shared memory holds meta then col then val.
+template <typename V>
+__device__ Tab<V> stage_tables(const Sell &m, const V *gval, const Range &R, int cache_cap, int meta_slots,
+                               unsigned char *dsm)
+{
+    Tab<V> t;
+    int2 *meta = reinterpret_cast<int2 *>(dsm);
+    int32_t *col = reinterpret_cast<int32_t *>(dsm + (size_t)meta_slots * sizeof(int2));
+    V *val = reinterpret_cast<V *>(dsm + (size_t)meta_slots * sizeof(int2) + (size_t)cache_cap * sizeof(int32_t));
+    const int nsl = R.s1 - R.s0;
+    for (int k = threadIdx.x; k < nsl; k += blockDim.x) {
+        const int b = __ldg(m.slice_ptr + R.s0 + k);
+        meta[k] = make_int2(b, (__ldg(m.slice_ptr + R.s0 + k + 1) - b) >> 5);
+    }
+    const int base0 = (nsl > 0) ? __ldg(m.slice_ptr + R.s0) : 0;
+    const int total = (nsl > 0) ? __ldg(m.slice_ptr + R.s1) - base0 : 0;
+    const int cap = min(total, cache_cap);
+    for (int k = threadIdx.x; k < cap; k += blockDim.x) {
+        col[k] = __ldg(m.col + base0 + k);
+        val[k] = __ldg(gval + base0 + k);
+    }
+    __syncthreads();
+    t.meta = meta;
+    t.col = col;
+    t.val = val;
+    t.gcol = m.col;
+    t.gval = gval;
+    t.s0 = R.s0;
+    t.base0 = base0;
+    t.end = base0 + cap;
+    return t;
 }
 
 // (A x)_i in FP64, difference form: sum_f gamma_f (x_i - x_j) + pin x_i.
@@ -323,14 +387,6 @@ __device__ __forceinline__ double apply64_diag(const Sell &m, Row rw, int lane, 
         for (int c = 0; c < CH; ++c) acc = fma(-gm[c], xj[c], acc);
     }
     return acc;
-}
-
-// FP32 diagonal D_i = pin_i + sum_f (float)gamma_f, summed in slot order.
-__device__ __forceinline__ float diag32(const Sell &m, Row rw, int lane, float pin_i)
-{
-    float d = pin_i;
-    for (int k = 0; k < rw.w; ++k) d += __ldg(m.val32 + rw.base + k * kSlice + lane);
-    return d;
 }
 
 // Final two passes shared by both kernels: the true FP64 residual (difference
@@ -404,26 +460,63 @@ __device__ void record_abort(const SolveArgs &a)
 
 enum Action : int { kGo = 0, kConverged = 1, kCheck = 2, kNotConverged = 3, kBreakdown = 4, kUpdate = 5, kRestart = 6 };
 
+// Thread 0: c = E^{-1} y, published in shared memory (FP64 and FP32).
+__device__ __forceinline__ void coarse_solve(const Coarse *co, int K, Shared &sh)
+{
+    (void)co;
+    for (int i = 0; i < K; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < K; ++j) t = fma(sh.Einv[i * kMaxCoarse + j], sh.y[j], t);
+        sh.c64[i] = t;
+        sh.c32[i] = (float)t;
+    }
+}
+
+// Copy E^{-1} into shared memory once per solve.
+__device__ __forceinline__ void stage_coarse(const Coarse *co, Shared &sh)
+{
+    for (int q = threadIdx.x; q < kMaxCoarse * kMaxCoarse; q += blockDim.x) sh.Einv[q] = co->Einv[q];
+}
+
+__device__ __forceinline__ void zero_bins(Shared &sh)
+{
+    if (threadIdx.x < kMaxCoarse) {
+        sh.zb32[threadIdx.x] = 0.0f;
+        sh.zb64[threadIdx.x] = 0.0;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP64 Jacobi-PCG
+// FP64 Jacobi(+coarse)-PCG
 // ---------------------------------------------------------------------------
-template <int CH, int TPB>
-__global__ void __launch_bounds__(TPB, 1) k_solve_fp64(SolveArgs a)
+template <int CH>
+__global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
 {
+    constexpr int U = 2;  // slices in flight per warp in the SpMV pass
     __shared__ Shared sh;
+    extern __shared__ __align__(16) unsigned char dsm[];
     Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
     const Range R = my_range(a.m.n_slices);
+    stage_coarse(a.coarse, sh);
+    const Tab<double> tab = stage_tables<double>(a.m, a.m.val64, R, a.cache_cap, a.meta_slots, dsm);
     const int n = a.m.n;
+    const int ref = a.prm->ref;
+    const int K = a.coarse->K;
+    const int rc = a.coarse->ref_comp;
+    const double pin64 = a.prm->pin64;
+    const int nx = a.coarse->n_cross;
     double *x = a.x64;  // gathered by the true-residual pass
     double *__restrict__ r = a.r64;
     double *p = a.p64;  // gathered by the SpMV: read by other CTAs, no nc loads
     double *__restrict__ q = a.q64;
     const double *__restrict__ dinv = a.dinv64;
-    // thread-0 scalar state
-    double bnorm = 1.0, rz = 0.0;
-    int checks = 0;
+    const int8_t *__restrict__ comp = a.comp;
+    // thread-0 scalar state (rr_ref: ||r||^2 when Z^T r was last summed exactly;
+    // best: smallest true relative residual seen at a check)
+    double bnorm = 1.0, rz = 0.0, rr_ref = 0.0, best = 1e300;
+    int checks = 0, stall = 0;
 
     if (a.use_x0) {
         for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
@@ -432,61 +525,156 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_fp64(SolveArgs a)
         }
         if (!grid_sync(g, sh)) { record_abort(a); return; }
     }
-    // r = b - A x, z = D^{-1} r, p = z
-    double v3[3] = {0.0, 0.0, 0.0};  // b.b, r.r, r.z
-    for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-        const int i = s * kSlice + R.lane;
-        if (i < n) {
-            const double bi = a.b[i];
-            double ri = bi;
-            if (a.use_x0) ri = bi - apply64_diag<CH>(a.m, row_of(a.m, s), R.lane, x, x[i], a.diag64[i]);
-            else x[i] = 0.0;
-            const double zi = dinv[i] * ri;
-            r[i] = ri;
-            p[i] = zi;
-            v3[0] += bi * bi;
-            v3[1] += ri * ri;
-            v3[2] += ri * zi;
+    // r = b - A x, p = z = M^{-1} r; with a coarse space the Jacobi part is
+    // written first and the coarse part added once Z^T r is known.
+    {
+        double v3[3] = {0.0, 0.0, 0.0};  // b.b, r.r, r.(D^{-1} r)
+        double zb[kMaxCoarse];
+#pragma unroll
+        for (int k = 0; k < kMaxCoarse; ++k) zb[k] = 0.0;
+        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+            const int i = s * kSlice + R.lane;
+            if (i < n) {
+                const double bi = a.b[i];
+                double ri = bi;
+                if (a.use_x0) ri = bi - apply64_diag<CH>(a.m, row_of(a.m, s), R.lane, x, x[i], a.diag64[i]);
+                else x[i] = 0.0;
+                const double zi = dinv[i] * ri;
+                r[i] = ri;
+                p[i] = zi;
+                v3[0] += bi * bi;
+                v3[1] += ri * ri;
+                v3[2] += ri * zi;
+                if (K > 0) {
+                    const int cm = comp[i];
+#pragma unroll
+                    for (int k = 0; k < kMaxCoarse; ++k) zb[k] += (cm == k) ? ri : 0.0;
+                }
+            }
+        }
+        block_sum_f64<3>(sh, v3);
+        block_sum_f64<kMaxCoarse>(sh, zb);
+        double t3[3 + kMaxCoarse];
+        {
+            double blk[3 + kMaxCoarse];
+            blk[0] = v3[0]; blk[1] = v3[1]; blk[2] = v3[2];
+            for (int k = 0; k < kMaxCoarse; ++k) blk[3 + k] = zb[k];
+            if (!grid_allreduce<3 + kMaxCoarse>(g, sh, blk, t3, 3 + K)) { record_abort(a); return; }
+        }
+        if (threadIdx.x == 0) {
+            bnorm = (t3[0] > 0.0) ? sqrt(t3[0]) : 1.0;
+            rz = t3[2];
+            rr_ref = t3[1];
+            for (int k = 0; k < K; ++k) sh.y[k] = t3[3 + k];
+            coarse_solve(a.coarse, K, sh);
+            for (int k = 0; k < K; ++k) rz = fma(sh.c64[k], sh.y[k], rz);
+            sh.ctl.action = (sqrt(t3[1]) / bnorm <= a.rtol) ? kConverged : kGo;
+        }
+        __syncthreads();
+        if (K > 0) {
+            for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+                const int i = s * kSlice + R.lane;
+                if (i < n && comp[i] >= 0) p[i] += sh.c64[comp[i]];
+            }
         }
     }
-    block_sum_f64<3>(sh, v3);
-    double t3[3];
-    if (!grid_allreduce<3>(g, sh, v3, t3)) { record_abort(a); return; }
-    if (threadIdx.x == 0) {
-        bnorm = (t3[0] > 0.0) ? sqrt(t3[0]) : 1.0;
-        rz = t3[2];
-        sh.ctl.action = (sqrt(t3[1]) / bnorm <= a.rtol) ? kConverged : kGo;
-    }
-    __syncthreads();
     int action = sh.ctl.action;
     int iters = 0, status = GFM_OK;
     while (action != kConverged) {
         if (iters >= a.max_iters) { status = GFM_ERR_NOT_CONVERGED; break; }
         if (!grid_sync(g, sh)) { record_abort(a); return; }  // p complete
-        // pass 1: q = A p, p.q
+        zero_bins(sh);
+        __syncthreads();
+        // pass 1: q = A p, p.q; Z^T q from the faces between coarse regions
         double v1[1] = {0.0};
-        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-            const int i = s * kSlice + R.lane;
-            if (i < n) {
-                const double pi = p[i];
-                const double qi = apply64_diag<CH>(a.m, row_of(a.m, s), R.lane, p, pi, a.diag64[i]);
-                q[i] = qi;
-                v1[0] += pi * qi;
+        for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw) {
+            int ii[U], base[U], w[U];
+            double pi[U], acc[U];
+            int wmax = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int s = sb + u * R.nw;
+                ii[u] = s * kSlice + R.lane;
+                base[u] = 0;
+                w[u] = 0;
+                const bool act = s < R.s1 && ii[u] < n;
+                if (act) {
+                    const Row rw = tab.row(s);
+                    base[u] = rw.base;
+                    w[u] = rw.w;
+                }
+                pi[u] = act ? p[ii[u]] : 0.0;
+                acc[u] = act ? a.diag64[ii[u]] * pi[u] : 0.0;
+                wmax = max(wmax, w[u]);
+            }
+            for (int k0 = 0; k0 < wmax; k0 += CH) {
+                int j[U][CH];
+                double gm[U][CH], pj[U][CH];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const bool ok = k0 + c < w[u];
+                        const int slot = base[u] + (k0 + c) * kSlice + R.lane;
+                        j[u][c] = ok ? tab.c(slot) : 0;
+                        gm[u][c] = ok ? tab.v(slot) : 0.0;
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) pj[u][c] = (k0 + c < w[u]) ? p[j[u][c]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) acc[u] = fma(-gm[u][c], pj[u][c], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (sb + u * R.nw < R.s1 && ii[u] < n) {
+                    q[ii[u]] = acc[u];
+                    v1[0] = fma(pi[u], acc[u], v1[0]);
+                    if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb64[rc], pin64 * pi[u]);  // pin term of Z^T A p
+                }
+            }
+        }
+        if (K > 0) {
+            // each CTA takes an even share of the cross faces, one per thread
+            const int f0 = (int)(((long long)nx * blockIdx.x) / gridDim.x);
+            const int f1 = (int)(((long long)nx * (blockIdx.x + 1)) / gridDim.x);
+            // taken by the CTA's last threads, whose warps hold the fewest slices
+            for (int t = f0 + (int)(blockDim.x - 1 - threadIdx.x); t < f1; t += blockDim.x) {
+                const CrossFace cf = a.cross[t];
+                const double val = cf.g64 * (p[cf.o] - p[cf.v]);
+                if (cf.a >= 0) atomicAdd(&sh.zb64[cf.a], val);
+                if (cf.b >= 0) atomicAdd(&sh.zb64[cf.b], -val);
             }
         }
         block_sum_f64<1>(sh, v1);
-        double t1[1];
-        if (!grid_allreduce<1>(g, sh, v1, t1)) { record_abort(a); return; }
+        double t1[1 + kMaxCoarse];
+        {
+            double blk[1 + kMaxCoarse];
+            blk[0] = v1[0];
+            for (int k = 0; k < kMaxCoarse; ++k) blk[1 + k] = sh.zb64[k];
+            if (K > 0) {
+                if (!grid_allreduce<1 + kMaxCoarse>(g, sh, blk, t1, 1 + K)) { record_abort(a); return; }
+            } else {
+                double b1[1] = {blk[0]}, o1[1];
+                if (!grid_allreduce<1>(g, sh, b1, o1)) { record_abort(a); return; }
+                t1[0] = o1[0];
+            }
+        }
         if (threadIdx.x == 0) {
             const double pq = t1[0];
             const bool ok = pq > 0.0 && isfinite(pq);
-            sh.ctl.alpha = ok ? rz / pq : 0.0;
+            const double alpha = ok ? rz / pq : 0.0;
+            sh.ctl.alpha = alpha;
             sh.ctl.action = ok ? kGo : kBreakdown;
+            for (int k = 0; k < K; ++k) sh.y[k] = fma(-alpha, t1[1 + k], sh.y[k]);
         }
         __syncthreads();
         if (sh.ctl.action == kBreakdown) { status = GFM_ERR_BREAKDOWN; break; }
         const double alpha = sh.ctl.alpha;
-        // pass 2: x += alpha p, r -= alpha q, z = D^{-1} r; r.z, r.r
+        // pass 2: x += alpha p, r -= alpha q, z = M^{-1} r; r.z, r.r
         double v2[2] = {0.0, 0.0};
         for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
             const int i = s * kSlice + R.lane;
@@ -494,9 +682,8 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_fp64(SolveArgs a)
                 x[i] = fma(alpha, p[i], x[i]);
                 const double ri = fma(-alpha, q[i], r[i]);
                 r[i] = ri;
-                const double zi = dinv[i] * ri;
-                v2[0] += ri * zi;
-                v2[1] += ri * ri;
+                v2[0] = fma(ri, dinv[i] * ri, v2[0]);  // r.(D^{-1} r); the coarse part is added below
+                v2[1] = fma(ri, ri, v2[1]);
             }
         }
         block_sum_f64<2>(sh, v2);
@@ -506,48 +693,120 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_fp64(SolveArgs a)
         if (threadIdx.x == 0) {
             if (sqrt(t2[1]) / bnorm <= a.rtol) {
                 sh.ctl.action = kCheck;
+            } else if (K > 0 && t2[1] <= 1e-2 * rr_ref) {
+                // the residual fell a decade since Z^T r was last summed:
+                // sum it exactly again so the recurrence cannot drift
+                sh.ctl.xavg = t2[0];
+                rr_ref = t2[1];
+                sh.ctl.action = kUpdate;
             } else {
-                sh.ctl.beta = t2[0] / rz;
-                rz = t2[0];
+                // z = D^{-1} r + Z E^{-1} y:  r.z = r.D^{-1}r + y.E^{-1}y
+                coarse_solve(a.coarse, K, sh);
+                double rzn = t2[0];
+                for (int k = 0; k < K; ++k) rzn = fma(sh.c64[k], sh.y[k], rzn);
+                sh.ctl.beta = rzn / rz;
+                rz = rzn;
                 sh.ctl.action = kGo;
             }
         }
         __syncthreads();
         action = sh.ctl.action;
+        if (action == kUpdate) {
+            double zb[kMaxCoarse];
+#pragma unroll
+            for (int k = 0; k < kMaxCoarse; ++k) zb[k] = 0.0;
+            for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+                const int i = s * kSlice + R.lane;
+                if (i < n) {
+                    const int cm = comp[i];
+                    const double ri = r[i];
+#pragma unroll
+                    for (int k = 0; k < kMaxCoarse; ++k) zb[k] += (cm == k) ? ri : 0.0;
+                }
+            }
+            block_sum_f64<kMaxCoarse>(sh, zb);
+            double ty[kMaxCoarse];
+            if (!grid_allreduce<kMaxCoarse>(g, sh, zb, ty, K)) { record_abort(a); return; }
+            if (threadIdx.x == 0) {
+                for (int k = 0; k < K; ++k) sh.y[k] = ty[k];
+                coarse_solve(a.coarse, K, sh);
+                double rzn = sh.ctl.xavg;
+                for (int k = 0; k < K; ++k) rzn = fma(sh.c64[k], sh.y[k], rzn);
+                sh.ctl.beta = rzn / rz;
+                rz = rzn;
+                sh.ctl.action = kGo;
+            }
+            __syncthreads();
+            action = sh.ctl.action;
+        }
         if (action == kCheck) {
             // confirm with the true residual; restart from it on a miss
             if (!grid_sync(g, sh)) { record_abort(a); return; }  // x complete
             double vt[2] = {0.0, 0.0};
+            double zb[kMaxCoarse];
+#pragma unroll
+            for (int k = 0; k < kMaxCoarse; ++k) zb[k] = 0.0;
             for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
                 const int i = s * kSlice + R.lane;
                 if (i < n) {
-                    const double ri = a.b[i] - apply64_diag<CH>(a.m, row_of(a.m, s), R.lane, x, x[i], a.diag64[i]);
+                    // the true residual in difference form (sum_f gamma_f (x_i - x_j)):
+                    // accurate to rounding of the differences, not of diag_i x_i
+                    const double ri = a.b[i] - apply64_diff<CH>(a.m, row_of(a.m, s), R.lane, x, x[i],
+                                                                i == ref ? pin64 : 0.0);
                     const double zi = dinv[i] * ri;
                     r[i] = ri;
                     p[i] = zi;
                     vt[0] += ri * zi;
                     vt[1] += ri * ri;
+                    if (K > 0) {
+                        const int cm = comp[i];
+#pragma unroll
+                        for (int k = 0; k < kMaxCoarse; ++k) zb[k] += (cm == k) ? ri : 0.0;
+                    }
                 }
             }
             block_sum_f64<2>(sh, vt);
-            double tt[2];
-            if (!grid_allreduce<2>(g, sh, vt, tt)) { record_abort(a); return; }
+            block_sum_f64<kMaxCoarse>(sh, zb);
+            double tt[2 + kMaxCoarse];
+            {
+                double blk[2 + kMaxCoarse];
+                blk[0] = vt[0]; blk[1] = vt[1];
+                for (int k = 0; k < kMaxCoarse; ++k) blk[2 + k] = zb[k];
+                if (!grid_allreduce<2 + kMaxCoarse>(g, sh, blk, tt, 2 + K)) { record_abort(a); return; }
+            }
             if (threadIdx.x == 0) {
                 ++checks;
                 rz = tt[0];
-                if (sqrt(tt[1]) / bnorm <= a.rtol) sh.ctl.action = kConverged;
-                else sh.ctl.action = (checks > a.max_refine) ? kNotConverged : kGo;
+                rr_ref = tt[1];
+                for (int k = 0; k < K; ++k) sh.y[k] = tt[2 + k];
+                coarse_solve(a.coarse, K, sh);
+                for (int k = 0; k < K; ++k) rz = fma(sh.c64[k], sh.y[k], rz);
+                const double rel = sqrt(tt[1]) / bnorm;
+                if (rel < 0.5 * best) { best = rel; stall = 0; }
+                else ++stall;
+                if (rel <= a.rtol) sh.ctl.action = kConverged;
+                else sh.ctl.action = (checks > a.max_refine || stall >= 3) ? kNotConverged : kGo;
             }
             __syncthreads();
             action = sh.ctl.action;
             if (action == kNotConverged) { status = GFM_ERR_NOT_CONVERGED; break; }
+            if (action == kGo && K > 0) {
+                for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+                    const int i = s * kSlice + R.lane;
+                    if (i < n && comp[i] >= 0) p[i] += sh.c64[comp[i]];
+                }
+            }
             continue;
         }
         const double beta = sh.ctl.beta;
         // pass 3: p = z + beta p
         for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
             const int i = s * kSlice + R.lane;
-            if (i < n) p[i] = fma(beta, p[i], dinv[i] * r[i]);
+            if (i < n) {
+                double zi = dinv[i] * r[i];
+                if (K > 0 && comp[i] >= 0) zi += sh.c64[comp[i]];
+                p[i] = fma(beta, p[i], zi);
+            }
         }
     }
     if (threadIdx.x == 0) sh.ctl.action = checks;
@@ -561,15 +820,17 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_fp64(SolveArgs a)
 namespace {
 
 // Residual replacement.  When `fold`, first x += e / sc in FP64 (e = 0).
-// Then r = b - A x in FP64 (difference form), r32 = (float)(r sc),
-// u = r32 / D into up.x; with `zero_p` the kept direction up.y is cleared.
-// t = (||r||^2 in FP64, r32.u, r32.r32).
+// Then r = b - A x in FP64 (difference form), r32 = (float)(r sc) and the
+// preconditioned residual u = r32 / D + (Z E^{-1} Z^T r32) into up.x; with
+// `zero_p` the kept direction up.y is cleared.  Thread 0 gets
+// t = (||r||^2 in FP64, r32.u, r32.r32) and sh.y = Z^T r32.
 template <int CH>
 __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, float2 *up, double sc,
                                  double isc, bool fold, bool zero_p, double (&t)[3])
 {
     const int n = a.m.n;
     const int ref = a.prm->ref;
+    const int K = a.coarse->K;
     const double pin64 = a.prm->pin64;
     double *x = a.x64;
     if (fold) {
@@ -583,7 +844,8 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
         if (!grid_sync(g, sh)) return false;  // x complete
     }
     double vr[1] = {0.0};
-    FF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    FF acc[2 + kMaxCoarse];
+    for (int k = 0; k < 2 + kMaxCoarse; ++k) acc[k] = FF{0.f, 0.f};
     for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
         const int i = s * kSlice + R.lane;
         if (i < n) {
@@ -597,30 +859,62 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
             else up[i].x = u;
             ff_add(acc[0], r32 * u);
             ff_add(acc[1], r32 * r32);
+            const int cm = a.comp[i];
+#pragma unroll
+            for (int k = 0; k < kMaxCoarse; ++k) ff_add(acc[2 + k], (cm == k) ? r32 : 0.0f);
         }
     }
     block_sum_f64<1>(sh, vr);
-    double ff2[2];
-    block_sum_ff<2>(sh, acc, ff2);
-    const double blk[3] = {vr[0], ff2[0], ff2[1]};
-    return grid_allreduce<3>(g, sh, blk, t);
+    double ffo[2 + kMaxCoarse];
+    block_sum_ff<2 + kMaxCoarse>(sh, acc, ffo);
+    double blk[3 + kMaxCoarse], tt[3 + kMaxCoarse];
+    blk[0] = vr[0];
+    for (int k = 0; k < 2 + kMaxCoarse; ++k) blk[1 + k] = ffo[k];
+    if (!grid_allreduce<3 + kMaxCoarse>(g, sh, blk, tt, 3 + K)) return false;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) sh.y[k] = tt[3 + k];
+        coarse_solve(a.coarse, K, sh);
+        double gam = tt[1];
+        for (int k = 0; k < K; ++k) gam = fma(sh.c64[k], sh.y[k], gam);
+        t[0] = tt[0];
+        t[1] = gam;
+        t[2] = tt[2];
+    }
+    __syncthreads();
+    if (K > 0) {
+        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+            const int i = s * kSlice + R.lane;
+            if (i < n && a.comp[i] >= 0) up[i].x += sh.c32[a.comp[i]];
+        }
+        if (!grid_sync(g, sh)) return false;  // u complete before it is gathered
+    }
+    return true;
 }
 
 }  // namespace
 
-template <int CH, int TPB>
-__global__ void __launch_bounds__(TPB, 1) k_solve_mixed(SolveArgs a)
+template <int CH>
+__global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 {
+    constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass
+    constexpr int UB = 4;       // slices in flight per warp in the update pass
     __shared__ Shared sh;
+    extern __shared__ __align__(16) unsigned char dsm[];
     Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
     const Range R = my_range(a.m.n_slices);
+    stage_coarse(a.coarse, sh);
+    const Tab<float> tab = stage_tables<float>(a.m, a.m.val32, R, a.cache_cap, a.meta_slots, dsm);
     const int n = a.m.n;
     const int ref = a.prm->ref;
     const float pin32 = a.prm->pin32;
+    const int K = a.coarse->K;
+    const int rc = a.coarse->ref_comp;
+    const int nx = a.coarse->n_cross;
     float *__restrict__ E = a.E;
     float *__restrict__ R32 = a.R32;
     float *__restrict__ S32 = a.S32;
     const float *__restrict__ dinv = a.dinv32;
+    const int8_t *__restrict__ comp = a.comp;
 
     // prologue: x0, e = 0, no direction yet, ||b||
     double vb[1] = {0.0};
@@ -636,9 +930,9 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_mixed(SolveArgs a)
     block_sum_f64<1>(sh, vb);
     double tb[1];
     if (!grid_allreduce<1>(g, sh, vb, tb)) { record_abort(a); return; }
-    // thread-0 scalar state
+    // thread-0 scalar state (last_upd: iteration of the last residual replacement)
     double bnorm = 1.0, gam = 0.0, gam_prev = 1.0, rho_max = 0.0, best_rel2 = 0.0, rho_stop = 0.0;
-    int stall = 0;
+    int stall = 0, last_upd = 0;
     if (threadIdx.x == 0) {
         bnorm = (tb[0] > 0.0) ? sqrt(tb[0]) : 1.0;
         // one power-of-two scale for the whole solve, from ||b||: residual
@@ -669,45 +963,98 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_mixed(SolveArgs a)
     int action = sh.ctl.action;
     while (action != kConverged) {
         const float be = sh.ctl.be;
+        zero_bins(sh);
+        __syncthreads();
         // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s
         FF accA[1] = {{0.f, 0.f}};
-        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-            const int i = s * kSlice + R.lane;
-            if (i < n) {
-                const Row rw = row_of(a.m, s);
-                const float2 v = cur[i];
-                const float pi = fmaf(be, v.y, v.x);
-                const float pin_i = (i == ref) ? pin32 : 0.0f;
-                float si = pin_i * pi;
-                for (int k0 = 0; k0 < rw.w; k0 += CH) {
-                    int j[CH];
-                    float gm[CH];
-                    float2 vj[CH];
+        for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw) {
+            int ii[U], base[U], w[U];
+            float2 v[U];
+            float pn[U], si[U];
+            int wmax = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int s = sb + u * R.nw;
+                ii[u] = s * kSlice + R.lane;
+                base[u] = 0;
+                w[u] = 0;
+                const bool act = s < R.s1 && ii[u] < n;
+                if (act) {
+                    const Row rw = tab.row(s);
+                    base[u] = rw.base;
+                    w[u] = rw.w;
+                }
+                v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
+                pn[u] = fmaf(be, v[u].y, v[u].x);
+                si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+                wmax = max(wmax, w[u]);
+            }
+            for (int k0 = 0; k0 < wmax; k0 += CH) {
+                int j[U][CH];
+                float gm[U][CH];
+                float2 vj[U][CH];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
-                        const bool ok = k0 + c < rw.w;
-                        const int slot = rw.base + (k0 + c) * kSlice + R.lane;
-                        j[c] = ok ? __ldg(a.m.col + slot) : 0;
-                        gm[c] = ok ? __ldg(a.m.val32 + slot) : 0.0f;
+                        const bool ok = k0 + c < w[u];
+                        const int slot = base[u] + (k0 + c) * kSlice + R.lane;
+                        j[u][c] = ok ? tab.c(slot) : 0;
+                        gm[u][c] = ok ? tab.v(slot) : 0.0f;
                     }
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) vj[c] = (k0 + c < rw.w) ? cur[j[c]] : v;
+                for (int u = 0; u < U; ++u)
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) si = fmaf(gm[c], pi - fmaf(be, vj[c].y, vj[c].x), si);
+                    for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (sb + u * R.nw < R.s1 && ii[u] < n) {
+                    nxt[ii[u]].y = pn[u];
+                    S32[ii[u]] = si[u];
+                    ff_add(accA[0], pn[u] * si[u]);
+                    if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
                 }
-                nxt[i].y = pi;
-                S32[i] = si;
-                ff_add(accA[0], pi * si);
             }
         }
-        double blkA[1], tA[1];
+        if (K > 0) {
+            // Z^T (A p) from the faces between coarse regions (+ the pin)
+            const int f0 = (int)(((long long)nx * blockIdx.x) / gridDim.x);
+            const int f1 = (int)(((long long)nx * (blockIdx.x + 1)) / gridDim.x);
+            // taken by the CTA's last threads, whose warps hold the fewest slices
+            for (int tf = f0 + (int)(blockDim.x - 1 - threadIdx.x); tf < f1; tf += blockDim.x) {
+                const CrossFace cf = a.cross[tf];
+                const float2 vo = cur[cf.o], vv = cur[cf.v];
+                const float val = cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
+                if (cf.a >= 0) atomicAdd(&sh.zb32[cf.a], val);
+                if (cf.b >= 0) atomicAdd(&sh.zb32[cf.b], -val);
+            }
+        }
+        double blkA[1], tA[1 + kMaxCoarse];
         block_sum_ff<1>(sh, accA, blkA);
-        if (!grid_allreduce<1>(g, sh, blkA, tA)) { record_abort(a); return; }
+        if (K > 0) {
+            double b9[1 + kMaxCoarse];
+            b9[0] = blkA[0];
+            for (int k = 0; k < kMaxCoarse; ++k) b9[1 + k] = (double)sh.zb32[k];
+            if (!grid_allreduce<1 + kMaxCoarse>(g, sh, b9, tA, 1 + K)) { record_abort(a); return; }
+        } else {
+            double o1[1];
+            if (!grid_allreduce<1>(g, sh, blkA, o1)) { record_abort(a); return; }
+            tA[0] = o1[0];
+        }
         if (threadIdx.x == 0) {
             const double ps = tA[0];
             const bool ok = ps > 0.0 && isfinite(ps) && gam > 0.0;
-            sh.ctl.al = ok ? (float)(gam / ps) : 0.0f;
+            const double alpha = ok ? gam / ps : 0.0;
+            sh.ctl.al = (float)alpha;
             sh.ctl.action = ok ? kGo : kRestart;
+            for (int k = 0; k < K; ++k) sh.y[k] = fma(-alpha, tA[1 + k], sh.y[k]);
+            coarse_solve(a.coarse, K, sh);
         }
         __syncthreads();
         if (sh.ctl.action == kRestart) {
@@ -728,19 +1075,36 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_mixed(SolveArgs a)
             continue;
         }
         const float al = sh.ctl.al;
-        // pass B: e += alpha p, r -= alpha s, u = D^{-1} r; r.u, r.r
+        // pass B: e += alpha p, r -= alpha s, u = M^{-1} r; r.u, r.r
         FF accB[2] = {{0.f, 0.f}, {0.f, 0.f}};
-        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-            const int i = s * kSlice + R.lane;
-            if (i < n) {
-                const float pi = nxt[i].y;
-                E[i] = fmaf(al, pi, E[i]);
-                const float ri = fmaf(-al, S32[i], R32[i]);
-                R32[i] = ri;
-                const float ui = ri * dinv[i];
-                nxt[i].x = ui;
-                ff_add(accB[0], ri * ui);
-                ff_add(accB[1], ri * ri);
+        for (int sb = R.s0 + R.warp; sb < R.s1; sb += UB * R.nw) {
+            int ii[UB];
+            bool act[UB];
+            float pi[UB], si[UB], ri[UB], ei[UB], di[UB];
+            int cm[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                ii[u] = (sb + u * R.nw) * kSlice + R.lane;
+                act[u] = sb + u * R.nw < R.s1 && ii[u] < n;
+                pi[u] = act[u] ? nxt[ii[u]].y : 0.f;
+                si[u] = act[u] ? S32[ii[u]] : 0.f;
+                ri[u] = act[u] ? R32[ii[u]] : 0.f;
+                ei[u] = act[u] ? E[ii[u]] : 0.f;
+                di[u] = act[u] ? dinv[ii[u]] : 0.f;
+                cm[u] = (act[u] && K > 0) ? (int)comp[ii[u]] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                if (act[u]) {
+                    E[ii[u]] = fmaf(al, pi[u], ei[u]);
+                    const float rn = fmaf(-al, si[u], ri[u]);
+                    R32[ii[u]] = rn;
+                    float un = rn * di[u];
+                    if (cm[u] >= 0) un += sh.c32[cm[u]];
+                    nxt[ii[u]].x = un;
+                    ff_add(accB[0], rn * un);
+                    ff_add(accB[1], rn * rn);
+                }
             }
         }
         double blkB[2], tB[2];
@@ -753,8 +1117,14 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_mixed(SolveArgs a)
             gam = tB[0];
             const double rho = tB[1];
             if (rho > rho_max) rho_max = rho;
+            // replacement when the FP32 residual fell a decade, claims
+            // convergence, or has not fallen a decade for 1000 iterations
+            // (a stagnating FP32 recurrence is then caught by the stall test)
             if (iters >= a.max_iters) sh.ctl.action = kNotConverged;
-            else if (rho <= 1e-2 * rho_max || rho <= rho_stop || !(gam > 0.0)) sh.ctl.action = kUpdate;
+            else if (rho <= 1e-2 * rho_max || rho <= rho_stop || !(gam > 0.0) || iters - last_upd >= 1000) {
+                sh.ctl.action = kUpdate;
+                last_upd = iters;
+            }
             else {
                 sh.ctl.be = (float)(gam / gam_prev);
                 sh.ctl.action = kGo;
@@ -792,20 +1162,441 @@ __global__ void __launch_bounds__(TPB, 1) k_solve_mixed(SolveArgs a)
     finish<CH>(a, g, sh, R, iters, updates, status, bnorm);
 }
 
-// Instantiations: faces per row chunk (4 for 2D hex meshes, 8 otherwise) and
-// the CTA size bound (512 threads may use up to 128 registers without spills;
-// 1024 threads are capped at 64).
-const void *solver_kernel(Mode m, int max_width, int threads)
+// ---------------------------------------------------------------------------
+// Batched mixed-precision solve: many independent tanks in one persistent
+// launch.  Every CTA works on one tank; per-tank scalars live in shared memory
+// and every CTA computes ALL tanks' sums and decisions from the same partials,
+// so all CTAs agree on the barrier schedule: a residual replacement runs (for
+// the tanks that need it) whenever any tank needs one, and finished tanks drop
+// out of the passes while the others iterate.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TankState {
+    double bnorm[kMaxTanks], sc[kMaxTanks], isc[kMaxTanks], gam[kMaxTanks], gam_prev[kMaxTanks];
+    double rho_max[kMaxTanks], best[kMaxTanks], rho_stop[kMaxTanks], xavg[kMaxTanks];
+    double tot[4][kMaxTanks];
+    float al[kMaxTanks], be[kMaxTanks];
+    int act[kMaxTanks];   // kGo while iterating, else kConverged / kNotConverged / kBreakdown
+    int flag[kMaxTanks];  // pending replacement: 0, kUpdate, kRestart, kNotConverged
+    int iters[kMaxTanks], updates[kMaxTanks], stall[kMaxTanks], last_upd[kMaxTanks], restarts[kMaxTanks];
+    int any_flag, any_active;
+};
+
+// Per-tank all-reduce: CTA partials as in grid_allreduce, then warp k sums
+// value k for every tank over that tank's CTAs (fixed order) into ts.tot[k].
+template <int NR>
+__device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &ts, const BatchArgs &bt,
+                                                const double (&blk)[NR])
 {
-    const bool big = threads > 512;
-    if (max_width <= 4) {
-        if (m == Mode::FP64) return big ? (const void *)k_solve_fp64<4, 1024> : (const void *)k_solve_fp64<4, 512>;
-        return big ? (const void *)k_solve_mixed<4, 1024> : (const void *)k_solve_mixed<4, 512>;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) g.partials[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
     }
-    if (m == Mode::FP64) return big ? (const void *)k_solve_fp64<8, 1024> : (const void *)k_solve_fp64<8, 512>;
-    return big ? (const void *)k_solve_mixed<8, 1024> : (const void *)k_solve_mixed<8, 512>;
+    if (!grid_sync(g, sh)) return false;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < NR; k += nw) {
+        const double *src = g.partials + ((size_t)g.parity * kMaxNR + k) * g.G;
+        for (int t = lane; t < bt.T; t += 32) {
+            const int2 r = bt.tank_cta[t];
+            double acc = 0.0;
+            for (int c = r.x; c < r.y; ++c) acc += __ldcg(src + c);
+            ts.tot[k][t] = acc;
+        }
+    }
+    g.parity ^= 1;
+    __syncthreads();
+    return true;
 }
 
-int solver_max_threads() { return 1024; }
+// Residual replacement for the tanks with a pending flag (or all, `all`):
+// x += e / sc (FP64, when `fold`), r = b - A x (FP64, difference form),
+// r32 = (float)(r sc), u = r32 / D into up (direction cleared on restart).
+// ts.tot = (||r||^2, r32.u, r32.r32) per tank.
+template <int CH>
+__device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, Shared &sh, TankState &ts,
+                              const Range &R, int tank, int cend, int ref, double pin64, float2 *up, bool fold,
+                              bool all)
+{
+    const bool work = all || ts.flag[tank] != 0;
+    const bool zero_p = all || ts.flag[tank] == kRestart;
+    const double sc = ts.sc[tank], isc = ts.isc[tank];
+    double *x = a.x64;
+    if (fold) {
+        if (work) {
+            for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+                const int i = s * kSlice + R.lane;
+                if (i < cend) {
+                    x[i] = fma((double)a.E[i], isc, x[i]);
+                    a.E[i] = 0.0f;
+                }
+            }
+        }
+        if (!grid_sync(g, sh)) return false;  // x complete
+    }
+    double vr[1] = {0.0};
+    FF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    if (work) {
+        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+            const int i = s * kSlice + R.lane;
+            if (i < cend) {
+                const double xi = x[i];
+                const double ri = a.b[i] - apply64_diff<CH>(a.m, row_of(a.m, s), R.lane, x, xi, i == ref ? pin64 : 0.0);
+                vr[0] = fma(ri, ri, vr[0]);
+                const float r32 = (float)(ri * sc);
+                const float u = r32 * a.dinv32[i];
+                a.R32[i] = r32;
+                if (zero_p) up[i] = make_float2(u, 0.0f);
+                else up[i].x = u;
+                ff_add(acc[0], r32 * u);
+                ff_add(acc[1], r32 * r32);
+            }
+        }
+    }
+    block_sum_f64<1>(sh, vr);
+    double ffo[2];
+    block_sum_ff<2>(sh, acc, ffo);
+    const double blk[3] = {vr[0], ffo[0], ffo[1]};
+    return batch_allreduce<3>(g, sh, ts, bt, blk);
+}
+
+__device__ void batch_abort(const SolveArgs &a, const BatchArgs &bt)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int e = ld_volatile_i32(a.err);
+        for (int t = 0; t < bt.T; ++t) {
+            bt.infos[t].status = e;
+            bt.infos[t].rel_res_l2 = -1.0;
+            bt.infos[t].rel_res_l1 = -1.0;
+        }
+    }
+}
+
+}  // namespace
+
+template <int CH>
+__global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs bt)
+{
+    constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass
+    constexpr int UB = 4;       // slices in flight per warp in the update pass
+    __shared__ Shared sh;
+    __shared__ TankState ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
+    const int4 me = bt.cta[blockIdx.x];
+    const int tank = me.x, cend = me.w;
+    Range R;
+    R.s0 = me.y;
+    R.s1 = me.z;
+    R.warp = threadIdx.x >> 5;
+    R.lane = threadIdx.x & 31;
+    R.nw = blockDim.x >> 5;
+    const Tab<float> tab = stage_tables<float>(a.m, a.m.val32, R, a.cache_cap, a.meta_slots, dsm);
+    const DevParams pm = bt.tprm[tank];
+    const int ref = pm.ref;
+    const float pin32 = pm.pin32;
+    const double pin64 = pm.pin64;
+    const int T = bt.T;
+    float *__restrict__ E = a.E;
+    float *__restrict__ R32 = a.R32;
+    float *__restrict__ S32 = a.S32;
+    const float *__restrict__ dinv = a.dinv32;
+    const double rtol2 = a.rtol * a.rtol;
+    const int cap_updates = a.max_refine + 1 + (int)(2.0 * log10(1.0 / a.rtol));
+
+    // prologue: x0, e = 0, ||b||^2 per tank
+    double vb[1] = {0.0};
+    for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+        const int i = s * kSlice + R.lane;
+        if (i < cend) {
+            a.x64[i] = a.use_x0 ? a.p_user[a.iperm[i]] : 0.0;
+            E[i] = 0.0f;
+            const double bi = a.b[i];
+            vb[0] += bi * bi;
+        }
+    }
+    block_sum_f64<1>(sh, vb);
+    if (!batch_allreduce<1>(g, sh, ts, bt, vb)) { batch_abort(a, bt); return; }
+    if (threadIdx.x < 32) {
+        for (int t = threadIdx.x; t < T; t += 32) {
+            const double bb = ts.tot[0][t];
+            const double bn = (bb > 0.0) ? sqrt(bb) : 1.0;
+            int ex;
+            frexp(bn / sqrt((double)(a.n_per_tank ? a.n_per_tank[t] : 1)), &ex);
+            ts.bnorm[t] = bn;
+            ts.sc[t] = ldexp(1.0, -ex);
+            ts.isc[t] = ldexp(1.0, ex);
+            ts.rho_stop[t] = rtol2 * (bn * ts.sc[t]) * (bn * ts.sc[t]);
+            ts.act[t] = kGo;
+            ts.flag[t] = 0;
+            ts.iters[t] = ts.updates[t] = ts.stall[t] = ts.last_upd[t] = ts.restarts[t] = 0;
+            ts.be[t] = 0.0f;
+            ts.gam_prev[t] = 1.0;
+        }
+    }
+    __syncthreads();
+    float2 *cur = a.UP0, *nxt = a.UP1;
+    if (!batch_replace<CH>(a, bt, g, sh, ts, R, tank, cend, ref, pin64, cur, false, true)) {
+        batch_abort(a, bt);
+        return;
+    }
+    if (threadIdx.x < 32) {
+        bool active = false;
+        for (int t = threadIdx.x; t < T; t += 32) {
+            const double rel2 = ts.tot[0][t] / (ts.bnorm[t] * ts.bnorm[t]);
+            ts.updates[t] = 1;
+            ts.best[t] = rel2;
+            ts.gam[t] = ts.tot[1][t];
+            ts.rho_max[t] = ts.tot[2][t];
+            ts.act[t] = (rel2 <= rtol2) ? kConverged : kGo;
+            active |= ts.act[t] == kGo;
+        }
+        active = __any_sync(0xffffffffu, active);
+        if (threadIdx.x == 0) ts.any_active = active;
+    }
+    __syncthreads();
+    while (ts.any_active) {
+        const bool work = ts.act[tank] == kGo;
+        const float be = ts.be[tank];
+        // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s
+        FF accA[1] = {{0.f, 0.f}};
+        if (work) {
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw) {
+                int ii[U], base[U], w[U];
+                float2 v[U];
+                float pn[U], si[U];
+                int wmax = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int s = sb + u * R.nw;
+                    ii[u] = s * kSlice + R.lane;
+                    base[u] = 0;
+                    w[u] = 0;
+                    const bool act = s < R.s1 && ii[u] < cend;
+                    if (act) {
+                        const Row rw = tab.row(s);
+                        base[u] = rw.base;
+                        w[u] = rw.w;
+                    }
+                    v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
+                    pn[u] = fmaf(be, v[u].y, v[u].x);
+                    si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+                    wmax = max(wmax, w[u]);
+                }
+                for (int k0 = 0; k0 < wmax; k0 += CH) {
+                    int j[U][CH];
+                    float gm[U][CH];
+                    float2 vj[U][CH];
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const bool ok = k0 + c < w[u];
+                            const int slot = base[u] + (k0 + c) * kSlice + R.lane;
+                            j[u][c] = ok ? tab.c(slot) : 0;
+                            gm[u][c] = ok ? tab.v(slot) : 0.0f;
+                        }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CH; ++c)
+                            si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (sb + u * R.nw < R.s1 && ii[u] < cend) {
+                        nxt[ii[u]].y = pn[u];
+                        S32[ii[u]] = si[u];
+                        ff_add(accA[0], pn[u] * si[u]);
+                    }
+                }
+            }
+        }
+        double blkA[1];
+        block_sum_ff<1>(sh, accA, blkA);
+        if (!batch_allreduce<1>(g, sh, ts, bt, blkA)) { batch_abort(a, bt); return; }
+        if (threadIdx.x < 32) {
+            for (int t = threadIdx.x; t < T; t += 32) {
+                if (ts.act[t] != kGo) continue;
+                const double ps = ts.tot[0][t];
+                const bool ok = ps > 0.0 && isfinite(ps) && ts.gam[t] > 0.0;
+                ts.al[t] = ok ? (float)(ts.gam[t] / ps) : 0.0f;
+                ts.flag[t] = ok ? 0 : kRestart;
+            }
+        }
+        __syncthreads();
+        const float al = ts.al[tank];
+        // pass B: e += alpha p, r -= alpha s, u = D^{-1} r; r.u, r.r
+        FF accB[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (work && ts.flag[tank] == 0) {
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += UB * R.nw) {
+                int ii[UB];
+                bool act[UB];
+                float pi[UB], si[UB], ri[UB], ei[UB], di[UB];
+#pragma unroll
+                for (int u = 0; u < UB; ++u) {
+                    ii[u] = (sb + u * R.nw) * kSlice + R.lane;
+                    act[u] = sb + u * R.nw < R.s1 && ii[u] < cend;
+                    pi[u] = act[u] ? nxt[ii[u]].y : 0.f;
+                    si[u] = act[u] ? S32[ii[u]] : 0.f;
+                    ri[u] = act[u] ? R32[ii[u]] : 0.f;
+                    ei[u] = act[u] ? E[ii[u]] : 0.f;
+                    di[u] = act[u] ? dinv[ii[u]] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < UB; ++u) {
+                    if (act[u]) {
+                        E[ii[u]] = fmaf(al, pi[u], ei[u]);
+                        const float rn = fmaf(-al, si[u], ri[u]);
+                        R32[ii[u]] = rn;
+                        const float un = rn * di[u];
+                        nxt[ii[u]].x = un;
+                        ff_add(accB[0], rn * un);
+                        ff_add(accB[1], rn * rn);
+                    }
+                }
+            }
+        }
+        double blkB[2];
+        block_sum_ff<2>(sh, accB, blkB);
+        if (!batch_allreduce<2>(g, sh, ts, bt, blkB)) { batch_abort(a, bt); return; }
+        { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
+        if (threadIdx.x < 32) {
+            bool any = false;
+            for (int t = threadIdx.x; t < T; t += 32) {
+                if (ts.act[t] != kGo) continue;
+                if (ts.flag[t] == kRestart) { any = true; continue; }
+                const int it = ++ts.iters[t];
+                ts.gam_prev[t] = ts.gam[t];
+                const double gam = ts.tot[0][t], rho = ts.tot[1][t];
+                ts.gam[t] = gam;
+                if (rho > ts.rho_max[t]) ts.rho_max[t] = rho;
+                if (it >= a.max_iters) {
+                    ts.flag[t] = kNotConverged;
+                } else if (rho <= 1e-2 * ts.rho_max[t] || rho <= ts.rho_stop[t] || !(gam > 0.0) ||
+                           it - ts.last_upd[t] >= 1000) {
+                    ts.flag[t] = kUpdate;
+                    ts.last_upd[t] = it;
+                } else {
+                    ts.be[t] = (float)(gam / ts.gam_prev[t]);
+                }
+                any |= ts.flag[t] != 0;
+            }
+            any = __any_sync(0xffffffffu, any);
+            if (threadIdx.x == 0) ts.any_flag = any;
+        }
+        __syncthreads();
+        if (ts.any_flag) {
+            // fold e into x and replace r by the true residual for the tanks
+            // that asked (restarts also clear their direction)
+            if (!batch_replace<CH>(a, bt, g, sh, ts, R, tank, cend, ref, pin64, cur, true, false)) {
+                batch_abort(a, bt);
+                return;
+            }
+            if (threadIdx.x < 32) {
+                for (int t = threadIdx.x; t < T; t += 32) {
+                    const int f = ts.flag[t];
+                    if (ts.act[t] != kGo || f == 0) continue;
+                    ts.flag[t] = 0;
+                    ++ts.updates[t];
+                    const double rel2 = ts.tot[0][t] / (ts.bnorm[t] * ts.bnorm[t]);
+                    if (rel2 <= rtol2) { ts.act[t] = kConverged; continue; }
+                    if (f == kNotConverged) { ts.act[t] = kNotConverged; continue; }
+                    if (f == kRestart) {
+                        if (++ts.restarts[t] > 3) { ts.act[t] = kBreakdown; continue; }
+                    } else {
+                        if (rel2 < 0.25 * ts.best[t]) { ts.best[t] = rel2; ts.stall[t] = 0; }
+                        else ++ts.stall[t];
+                    }
+                    if (ts.stall[t] > 8 || ts.updates[t] > cap_updates) { ts.act[t] = kNotConverged; continue; }
+                    ts.gam[t] = ts.tot[1][t];
+                    ts.rho_max[t] = ts.tot[2][t];
+                    ts.be[t] = (f == kRestart || !(ts.gam_prev[t] > 0.0)) ? 0.0f
+                                                                           : (float)(ts.gam[t] / ts.gam_prev[t]);
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < 32) {
+            bool active = false;
+            for (int t = threadIdx.x; t < T; t += 32) active |= ts.act[t] == kGo;
+            active = __any_sync(0xffffffffu, active);
+            if (threadIdx.x == 0) ts.any_active = active;
+        }
+        __syncthreads();
+    }
+    // per-tank finish: true residual, solution in caller order, L1 residual
+    if (!grid_sync(g, sh)) { batch_abort(a, bt); return; }
+    double v[2] = {0.0, 0.0};
+    for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+        const int i = s * kSlice + R.lane;
+        if (i < cend) {
+            const double xi = a.x64[i];
+            const double r = a.b[i] - apply64_diff<CH>(a.m, row_of(a.m, s), R.lane, a.x64, xi, i == ref ? pin64 : 0.0);
+            a.r64[i] = r;
+            v[0] += r * r;
+            v[1] += xi;
+        }
+    }
+    block_sum_f64<2>(sh, v);
+    if (!batch_allreduce<2>(g, sh, ts, bt, v)) { batch_abort(a, bt); return; }
+    if (threadIdx.x < 32) {
+        for (int t = threadIdx.x; t < T; t += 32) {
+            ts.xavg[t] = ts.tot[1][t] / (double)(a.n_per_tank ? a.n_per_tank[t] : 1);
+            ts.best[t] = ts.tot[0][t];  // ||r||^2, kept for the record
+        }
+    }
+    __syncthreads();
+    const double xavg = ts.xavg[tank];
+    double w[2] = {0.0, 0.0};
+    for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+        const int i = s * kSlice + R.lane;
+        if (i < cend) {
+            const double xi = a.x64[i];
+            a.p_user[a.iperm[i]] = xi;
+            const double r = a.r64[i];
+            const double rs = (i == ref) ? pin64 : 0.0;
+            const double Ax = a.b[i] - r;
+            w[0] += fabs(r);
+            w[1] += fabs(Ax - xavg * rs) + fabs(a.b[i] - xavg * rs);
+        }
+    }
+    block_sum_f64<2>(sh, w);
+    if (!batch_allreduce<2>(g, sh, ts, bt, w)) { batch_abort(a, bt); return; }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const int e = ld_volatile_i32(a.err);
+        for (int t = threadIdx.x; t < T; t += 32) {
+            int st = GFM_OK;
+            if (ts.act[t] == kNotConverged) st = GFM_ERR_NOT_CONVERGED;
+            else if (ts.act[t] == kBreakdown) st = GFM_ERR_BREAKDOWN;
+            if (e != 0) st = e;
+            bt.infos[t].iters = ts.iters[t];
+            bt.infos[t].refinements = ts.updates[t];
+            bt.infos[t].status = st;
+            bt.infos[t].reserved = 0;
+            bt.infos[t].rel_res_l2 = sqrt(ts.best[t]) / ts.bnorm[t];
+            bt.infos[t].rel_res_l1 = ts.tot[0][t] / (ts.tot[1][t] + 1e-300);
+        }
+    }
+}
+
+const void *batched_kernel(int max_width)
+{
+    return max_width <= 4 ? (const void *)k_solve_batched<4> : (const void *)k_solve_batched<8>;
+}
+
+// Instantiations by faces per row chunk: 4 for 2D hex meshes, 8 otherwise.
+const void *solver_kernel(Mode m, int max_width, int threads)
+{
+    (void)threads;
+    if (max_width <= 4) return m == Mode::FP64 ? (const void *)k_solve_fp64<4> : (const void *)k_solve_mixed<4>;
+    return m == Mode::FP64 ? (const void *)k_solve_fp64<8> : (const void *)k_solve_mixed<8>;
+}
+
+int solver_max_threads() { return 512; }
 
 }  // namespace gfm

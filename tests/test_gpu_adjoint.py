@@ -1,0 +1,112 @@
+"""GPU adjoint (reverse mode through solve and assembly) against the CPU
+oracle's gradient and against central finite differences of GPU solves."""
+import numpy as np
+import pytest
+import torch
+
+import cases
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _g():
+    import paper_1804_01130_gb300 as g
+    return g
+
+
+def _band(c, x0, x1, y0, y1):
+    return np.where((c.C[0] >= x0) & (c.C[0] <= x1) & (c.C[1] >= y0) & (c.C[1] <= y1), c.V, 0.0)
+
+
+def _setup(c, renumber=1):
+    s = _g().GFM.from_case(c, renumber=renumber)
+    s.assemble(torch.as_tensor(c.alpha), torch.as_tensor(c.phi), c.rho_w, c.rho_a, c.g, c.ref_cell, c.ref_value)
+    return s
+
+
+@pytest.mark.parametrize("name,mk", [
+    ("config1", lambda: cases.make_case(1)),
+    ("box_perm", lambda: cases.box_case(12, 8, 4, seed=6, permute=True, alpha_noise=0.05)),
+])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_adjoint_matches_oracle(name, mk, mode):
+    c = mk()
+    w = _band(c, 0.5, 1.5, 0.35, 0.65) if c.dims[2] == 1 else np.where(np.abs(c.C[1] - 0.5) < 0.15, c.V, 0.0)
+    dphi_ref, dalpha_ref, mu_ref, p_ref = oracle.adjoint(c, w, direct=c.n <= 2048, rtol=1e-14)
+    s = _setup(c)
+    p, _, _ = s.solve(mode="fp64", rtol=1e-13)
+    dphi, dalpha, mu, info = s.adjoint(p, torch.as_tensor(w), mode=mode, rtol=1e-12)
+    assert info.status == 0
+    scale_mu = np.abs(mu_ref).max()
+    assert np.max(np.abs(mu.cpu().numpy() - mu_ref)) <= 1e-7 * scale_mu
+    for got, ref in ((dphi, dphi_ref), (dalpha, dalpha_ref)):
+        g_ = got.cpu().numpy()
+        assert np.max(np.abs(g_ - ref)) <= 1e-5 * np.abs(ref).max()
+
+
+def test_autograd_function_backward():
+    g = _g()
+    c = cases.make_case(1)
+    s = g.GFM.from_case(c)
+    alpha = torch.as_tensor(c.alpha).cuda().requires_grad_(True)
+    phi = torch.as_tensor(c.phi).cuda().requires_grad_(True)
+    w = torch.as_tensor(_band(c, 0.5, 1.5, 0.35, 0.65)).cuda()
+    phys = dict(rho_w=c.rho_w, rho_a=c.rho_a, g=c.g, ref_cell=c.ref_cell)
+    p = g.GFMSolve.apply(alpha, phi, s, phys, dict(mode="mixed", rtol=1e-12))
+    loss = (w * p).sum()
+    loss.backward()
+    dphi_ref, dalpha_ref, _, _ = oracle.adjoint(c, w.cpu().numpy(), direct=True)
+    assert np.max(np.abs(phi.grad.cpu().numpy() - dphi_ref)) <= 1e-5 * np.abs(dphi_ref).max()
+    assert np.max(np.abs(alpha.grad.cpu().numpy() - dalpha_ref)) <= 1e-5 * np.abs(dalpha_ref).max()
+
+
+def test_adjoint_vs_central_differences_tank():
+    """Deck-band loss on the 1024x512 tank: 16 face-flux and 16 alpha
+    entries against central differences of FP64 GPU solves (eps = 1e-6 on
+    alpha; phi enters the source affinely, so a central difference is exact
+    for any step and the step is 100 max|phi|, far above the solves' noise)."""
+    c = cases.make_case(5)
+    w = _band(c, 7.5, 8.5, 1.9, 2.1)
+    s = _setup(c)
+    p, _, info = s.solve(mode="fp64", rtol=1e-13)
+    assert info.status == 0
+    # the adjoint source is a volume band: ||A|| ||mu|| / ||w|| is of the order of
+    # the condition number, so its attainable relative residual is ~1e-10
+    dphi, dalpha, _, ainfo = s.adjoint(p, torch.as_tensor(w), mode="mixed", rtol=2e-10)
+    assert ainfo.status == 0
+    dphi, dalpha = dphi.cpu().numpy(), dalpha.cpu().numpy()
+    wt = torch.as_tensor(w).cuda()
+    alpha0 = torch.as_tensor(c.alpha).cuda()
+    phi0 = torch.as_tensor(c.phi).cuda()
+
+    def L(alpha, phi):
+        s.assemble(alpha, phi, c.rho_w, c.rho_a, c.g, c.ref_cell)
+        pp, _, inf = s.solve(mode="fp64", rtol=1e-14, p0=p, max_refine=5, raise_on_error=False)
+        return float((wt * pp).sum())
+
+    rng = np.random.default_rng(1005)
+    band_cells = np.nonzero(w)[0]
+    band_faces = np.nonzero(np.isin(c.owner, band_cells) | np.isin(c.neighbour, band_cells))[0]
+    step = 100.0 * float(np.abs(c.phi).max())
+    worst = 0.0
+    for f in rng.choice(band_faces, 16, replace=False):
+        e = torch.zeros(c.F, dtype=torch.float64, device="cuda")
+        e[int(f)] = step
+        fd = (L(alpha0, phi0 + e) - L(alpha0, phi0 - e)) / (2 * step)
+        rel = abs(fd - dphi[f]) / max(abs(dphi[f]), 1e-3 * np.abs(dphi).max())
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (f, fd, dphi[f], rel)
+    fc = oracle.faces(c)
+    ifc = np.nonzero(fc.kind >= 2)[0]
+    cand = np.unique(np.concatenate([c.owner[ifc], c.neighbour[ifc]]))
+    cand = cand[(np.abs(c.alpha[cand] - 0.5) > 1e-3) & (w[cand] > 0)]
+    eps = 1e-6
+    for i in rng.choice(cand, min(16, cand.size), replace=False):
+        e = torch.zeros(c.n, dtype=torch.float64, device="cuda")
+        e[int(i)] = eps
+        fd = (L(alpha0 + e, phi0) - L(alpha0 - e, phi0)) / (2 * eps)
+        rel = abs(fd - dalpha[i]) / max(abs(dalpha[i]), 1e-3 * np.abs(dalpha).max())
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (i, fd, dalpha[i], rel)
+    print(f"adjoint vs central differences, worst relative deviation {worst:.2e}")

@@ -92,6 +92,12 @@ def test_argument_errors():
     with pytest.raises(g.GFMError) as e:
         s.set_tuning(threads=100)
     assert e.value.status == g.GFM_ERR_ARG
+    with pytest.raises(g.GFMError) as e:
+        s.set_tuning(threads=1024)
+    assert e.value.status == g.GFM_ERR_ARG
+    with pytest.raises(g.GFMError) as e:
+        s.set_coarse(9)
+    assert e.value.status == g.GFM_ERR_ARG
     # bad mesh: owner >= neighbour
     with pytest.raises(g.GFMError) as e:
         g.GFM(c.neighbour, c.owner, c.Sf, c.C)
@@ -157,8 +163,70 @@ def test_tuning_shapes_agree():
     c = cases.box_case(40, 20, 1, seed=2)
     s = _setup(c)
     ref, _, _ = s.solve(mode="mixed", rtol=1e-12)
-    for threads, per in [(256, 2), (512, 1), (1024, 1), (128, 4)]:
+    for threads, per in [(256, 2), (512, 1), (128, 4), (64, 8)]:
         s.set_tuning(threads, per)
         p, _, info = s.solve(mode="mixed", rtol=1e-12)
         assert info.status == 0
         assert np.linalg.norm((p - ref).cpu().numpy()) <= 1e-7 * np.linalg.norm(ref.cpu().numpy())
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_coarse_space_regions_and_speedup(mode):
+    """The two-level preconditioner finds one water and one air region on
+    the tank, cuts the iteration count, and changes nothing in the answer."""
+    c = cases.make_case(1)
+    p_ref, _, _, _ = oracle.solve(c, direct=True)
+    s = _setup(c)
+    k, nreg, sizes = s.coarse_info()
+    wet = int((c.alpha >= 0.5).sum())
+    assert k == 2 and nreg == 2 and sorted(sizes) == sorted([wet, c.n - wet])
+    p1, _, i1 = s.solve(mode=mode, rtol=1e-12)
+    s.set_coarse(0)
+    s.assemble(torch.as_tensor(c.alpha), torch.as_tensor(c.phi), c.rho_w, c.rho_a, c.g, c.ref_cell)
+    assert s.coarse_info()[0] == 0
+    p0, _, i0 = s.solve(mode=mode, rtol=1e-12)
+    assert i1.status == 0 and i0.status == 0
+    assert i1.iters < i0.iters
+    for p in (p0, p1):
+        assert np.linalg.norm(p.cpu().numpy() - p_ref) <= 1e-9 * np.linalg.norm(p_ref)
+
+
+def test_coarse_space_many_regions_and_unpinned():
+    """Floating droplets and bubbles give several regions; the kept ones are
+    the largest; an unpinned system falls back to Jacobi."""
+    c = cases.box_case(48, 32, 1, seed=5)
+    rng = np.random.default_rng(2)
+    a = c.alpha.copy()
+    i = np.arange(c.n) % 48
+    j = np.arange(c.n) // 48
+    for (ci, cj, r, val) in [(10, 26, 3, 1.0), (30, 28, 2, 1.0), (20, 6, 3, 0.0), (40, 5, 2, 0.0)]:
+        a[(i - ci) ** 2 + (j - cj) ** 2 <= r * r] = val
+    c.alpha = a
+    p_ref, _, _, _ = oracle.solve(c, direct=False, rtol=1e-14)
+    s = _g().GFM.from_case(c)
+    s.set_coarse(8, 4)
+    s.assemble(torch.as_tensor(c.alpha), torch.as_tensor(c.phi), c.rho_w, c.rho_a, c.g, c.ref_cell)
+    k, nreg, sizes = s.coarse_info()
+    assert k == nreg and k >= 5
+    assert sizes == sorted(sizes, reverse=True)
+    for mode in ("fp64", "mixed"):
+        p, _, info = s.solve(mode=mode, rtol=1e-12)
+        assert info.status == 0
+        assert np.linalg.norm(p.cpu().numpy() - p_ref) <= 1e-7 * np.linalg.norm(p_ref)
+    s.assemble(torch.as_tensor(c.alpha), torch.as_tensor(c.phi), c.rho_w, c.rho_a, c.g, -1)
+    assert s.coarse_info()[0] == 0
+    p, _, info = s.solve(mode="fp64", rtol=1e-11)
+    assert info.status == 0
+
+
+def test_profiling_leaves_no_stale_error():
+    """Reading the profile before any solve, then destroying the handle, must
+    not poison the next handle's launches."""
+    c = cases.box_case(16, 8, 1)
+    s = _setup(c)
+    s.set_profiling(True)
+    s.profile()
+    s.close()
+    s2 = _setup(c, renumber=2)
+    p, _, info = s2.solve(mode="mixed", rtol=1e-11)
+    assert info.status == 0
