@@ -271,7 +271,7 @@ class GFM:
         return p, fc, si
 
     def adjoint(self, p: torch.Tensor, dL_dp: torch.Tensor, mode="fp64", rtol=1e-12, inner_rtol=1e-4,
-                max_iters=1_000_000, timeout_ms=2000.0, stream=None):
+                max_iters=1_000_000, max_refine=30, timeout_ms=2000.0, raise_on_error=True, stream=None):
         """Returns (dL/dphi [F], dL/dalpha [n], mu [n], SolveInfo)."""
         d = self.device
         p = _f64(p, d)
@@ -279,11 +279,13 @@ class GFM:
         dphi = torch.empty(self.F, dtype=torch.float64, device=d)
         dalpha = torch.empty(self.n, dtype=torch.float64, device=d)
         mu = torch.empty(self.n, dtype=torch.float64, device=d)
-        o = self.make_opts(mode, rtol, inner_rtol, max_iters, 30, False, False, timeout_ms)
+        o = self.make_opts(mode, rtol, inner_rtol, max_iters, max_refine, False, False, timeout_ms)
         info = _Info()
         st = self.lib.gfm_solve_adjoint(self.h, ct.byref(o), _ptr(p), _ptr(g), _ptr(dphi), _ptr(dalpha), _ptr(mu),
                                         ct.byref(info), _stream(stream))
-        self._check(st, "gfm_solve_adjoint")
+        if st != GFM_OK and (raise_on_error or st not in (GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN,
+                                                          GFM_ERR_TIMEOUT)):
+            self._check(st, "gfm_solve_adjoint")
         return dphi, dalpha, mu, SolveInfo(info.iters, info.refinements, info.status, info.rel_res_l2,
                                            info.rel_res_l1)
 
