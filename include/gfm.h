@@ -251,6 +251,50 @@ gfm_status gfm_solve_adjoint(gfm_handle h, const gfm_solve_opts *opts, const dou
 gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *phi_host, const gfm_phys *phys,
                           const gfm_solve_opts *opts, double *p_host, gfm_solve_info *info, gfm_stream stream);
 
+/*
+ * Solve without device allocation.  The paper has no counterpart: this is an
+ * entry point for callers that cannot call cudaMalloc -- code running inside
+ * a host program that owns the GPU's memory (a CFD code or plugin drawing
+ * from the host's pool or held under a memory cap, where a cudaMalloc would
+ * be refused or fragment the pool) and loops that must not call
+ * cudaMalloc/cudaFree because those can synchronise the device.  It needs no
+ * handle (gfm_create allocates) and allocates nothing, on the device or
+ * through any library.
+ *
+ * Solves A x = b by FP64 Jacobi-preconditioned CG for a symmetric positive
+ * definite A in CSR form, all DEVICE pointers owned by the caller:
+ *   row_ptr [n+1], col [nnz], val [nnz] (int32, int32, FP64); every row
+ *   holds a positive diagonal entry.  The GFM system of gfm_assemble is
+ *   A_ii = diag_i, A_{own,nb} = A_{nb,own} = -gamma_f (gfm_export_system).
+ *   b [n] the right-hand side, x [n] the solution (in: the start vector when
+ *   use_x0 = 1).  x may not alias the other arrays.
+ * Stops when the TRUE residual ||b - A x||_2 <= rtol ||b||_2, after
+ * max_iters CG iterations, or after 30 restarts from the true residual.
+ * timeout_ms bounds each grid-barrier wait as in gfm_solve_opts.  info
+ * (nullable) is a DEVICE pointer to one record, written by the kernel
+ * (status GFM_OK, GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN, GFM_ERR_TIMEOUT,
+ * or GFM_ERR_ARG for a row without a positive diagonal).  The call only
+ * enqueues work on `stream` and never synchronises.
+ *
+ * Scratch: the CG vectors, the per-CTA partial sums and the barrier counter
+ * live in one fixed array in the library's device code, 8.05 MiB for
+ * n <= GFM_NOALLOC_MAX_CELLS; every GPU that loads the library's device code
+ * holds it until the process exits.  n beyond that limit returns
+ * GFM_ERR_ARG before anything is enqueued.  The first call on a device looks
+ * up the array's address and the co-resident grid size for that device
+ * (cudaGetSymbolAddress, with the caller's current device); make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * the barrier block is cleared on `stream` at every call, and the rest is
+ * written before it is read, but two calls whose work overlaps on the GPU
+ * (different streams or host threads) race on it and corrupt each other.
+ * Returns GFM_OK once enqueued, GFM_ERR_ARG (n out of range, NULL array,
+ * rtol <= 0, max_iters < 0, timeout_ms <= 0), GFM_ERR_CUDA.
+ */
+#define GFM_NOALLOC_MAX_CELLS 262144
+gfm_status gfm_solve_csr_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
+                                 const double *b, double *x, double rtol, int32_t max_iters, int32_t use_x0,
+                                 double timeout_ms, gfm_solve_info *info, gfm_stream stream);
+
 /* Launch shape of the persistent kernels (threads a multiple of 32, at most
  * 512).  threads = 0 / ctas_per_sm = 0 keep the current value.  Errors:
  * GFM_ERR_ARG if the shape is out of range or cannot be co-resident. */

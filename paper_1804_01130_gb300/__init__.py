@@ -18,6 +18,7 @@ from . import build as _build
 
 __all__ = [
     "GFMError", "SolveInfo", "Profile", "GFM", "GFMBatch", "GFMSolve", "load_library", "library_path",
+    "solve_csr_noalloc", "NOALLOC_MAX_CELLS",
     "GFM_OK", "GFM_ERR_ARG", "GFM_ERR_CUDA", "GFM_ERR_NOMEM", "GFM_ERR_NOT_CONVERGED", "GFM_ERR_BREAKDOWN",
     "GFM_ERR_TIMEOUT", "GFM_ERR_INCOMPATIBLE", "GFM_ERR_STATE", "EXPORTED_SYMBOLS",
 ]
@@ -31,8 +32,11 @@ EXPORTED_SYMBOLS = (
     "gfm_default_opts", "gfm_create", "gfm_destroy", "gfm_assemble", "gfm_export_system", "gfm_solve",
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
-    "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched",
+    "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc",
 )
+
+# largest n accepted by gfm_solve_csr_noalloc (its fixed device scratch)
+NOALLOC_MAX_CELLS = 262144
 
 
 class GFMError(RuntimeError):
@@ -127,6 +131,7 @@ def load_library(build_if_missing: bool = True):
         "gfm_get_permutation": ([P, P], S),
         "gfm_set_coarse": ([P, I, I], S),
         "gfm_get_coarse": ([P, ct.POINTER(I), ct.POINTER(I), P, P], S),
+        "gfm_solve_csr_noalloc": ([I, P, P, P, P, P, ct.c_double, I, I, ct.c_double, P, P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
     }
@@ -456,3 +461,35 @@ class GFMBatch(GFM):
         raw = t.detach().cpu().numpy().tobytes()
         rec = (_Info * self.T).from_buffer_copy(raw)
         return [SolveInfo(i.iters, i.refinements, i.status, i.rel_res_l2, i.rel_res_l1) for i in rec]
+
+
+def solve_csr_noalloc(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, b: torch.Tensor,
+                      x: torch.Tensor | None = None, rtol: float = 1e-10, max_iters: int = 1_000_000,
+                      use_x0: bool = False, timeout_ms: float = 2000.0, info: torch.Tensor | None = None,
+                      stream=None):
+    """FP64 Jacobi-PCG of a CSR system through gfm_solve_csr_noalloc, which
+    allocates no device memory (for callers that cannot; its temporaries sit
+    in a fixed device array of the library, n <= NOALLOC_MAX_CELLS).  All
+    tensors are caller-owned CUDA tensors (int32 row_ptr/col, FP64 val/b/x);
+    x and info (a 32-byte uint8 device tensor for the result record) are made
+    here when not given.  Returns (x, info tensor); read the record with
+    GFM.info_from_device.  Enqueues only: nothing is synchronised."""
+    lib = load_library()
+    n = int(b.numel())
+    if x is None:
+        x = torch.zeros(n, dtype=torch.float64, device=b.device)
+    if info is None:
+        info = torch.zeros(ct.sizeof(_Info), dtype=torch.uint8, device=b.device)
+    for t, dt in ((row_ptr, torch.int32), (col, torch.int32), (val, torch.float64), (b, torch.float64),
+                  (x, torch.float64)):
+        if t.dtype != dt:
+            raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: expected {dt}, got {t.dtype}")
+    st = lib.gfm_solve_csr_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x), float(rtol),
+                                   int(max_iters), int(bool(use_x0)), float(timeout_ms), _ptr(info),
+                                   _stream(stream))
+    if st != GFM_OK:
+        why = (f"n = {n} is outside 1..{NOALLOC_MAX_CELLS}, the capacity of its fixed device scratch"
+               if st == GFM_ERR_ARG and not 1 <= n <= NOALLOC_MAX_CELLS else
+               lib.gfm_status_string(st).decode())
+        raise GFMError(st, f"gfm_solve_csr_noalloc: {why}")
+    return x, info

@@ -27,6 +27,7 @@ UNITS = {
     "gfm_solve.cu": ["-Xptxas", "-v"],
     "gfm_coarse.cu": [],
     "gfm_setup.cpp": [],
+    "gfm_noalloc.cu": ["-Xptxas", "-v"],
 }
 HEADERS = ["gfm_internal.h", "gfm_setup.h"]
 
