@@ -103,6 +103,8 @@ def test_adjoint_vs_central_differences_tank():
         rel = abs(fd - dphi[f]) / max(abs(dphi[f]), 1e-3 * np.abs(dphi).max())
         worst = max(worst, rel)
         assert rel <= 1e-5, (f, fd, dphi[f], rel)
+    print(f"dL/dphi vs central differences, worst relative deviation {worst:.2e}")
+    worst = 0.0
     fc = oracle.faces(c)
     ifc = np.nonzero(fc.kind >= 2)[0]
     cand = np.unique(np.concatenate([c.owner[ifc], c.neighbour[ifc]]))
@@ -121,4 +123,65 @@ def test_adjoint_vs_central_differences_tank():
         rel = abs(fd - dalpha[i]) / abs(dalpha[i])
         worst = max(worst, rel)
         assert rel <= 1e-4, (i, fd, dalpha[i], rel)
-    print(f"adjoint vs central differences, worst relative deviation {worst:.2e}")
+    print(f"dL/dalpha vs Richardson central differences, worst relative deviation {worst:.2e}")
+
+
+def test_adjoint_alpha_central_differences_eps_1e6_tank():
+    """Central differences with eps = 1e-6 on 16 alpha entries of the
+    deck-band loss, at the 1e-5 bar.  At this step the difference of two full
+    solves is below their noise, so the change of L comes from an identity
+    that holds for any fixed p0: L(alpha') = w.p0 + mu'.(b' - A' p0), with
+    mu' = A'^{-1} w solved on the GPU after assembling at alpha'.  b' - A' p0
+    is split into r0 = b - A p0 and its change, which the exported face and
+    cell coefficients give to rounding (it is nonzero only around the
+    perturbed cell), so the difference quotient carries the adjoint solves'
+    relative error instead of the forward solves' absolute noise."""
+    c = cases.make_case(5)
+    w = _band(c, 7.5, 8.5, 1.9, 2.1)
+    s = _setup(c)
+    p, _, info = s.solve(mode="fp64", rtol=1e-13)
+    assert info.status == 0
+    wt = torch.as_tensor(w).cuda()
+    _, dalpha, _, ainfo = s.adjoint(p, wt, mode="fp64", rtol=1e-10)
+    assert ainfo.status == 0
+    dalpha = dalpha.cpu().numpy()
+    ex0 = {k: v.cpu().numpy() for k, v in s.export_system().items()}
+    p0 = p.cpu().numpy()
+    own, nb = c.owner, c.neighbour
+
+    def apply(diag, gamma, x):  # face-form A x on the host, fixed order
+        y = diag * x
+        y -= np.bincount(own, weights=gamma * x[nb], minlength=c.n)
+        y -= np.bincount(nb, weights=gamma * x[own], minlength=c.n)
+        return y
+
+    r0 = ex0["b"] - apply(ex0["diag"], ex0["gamma"], p0)
+    alpha0 = torch.as_tensor(c.alpha).cuda()
+    phi0 = torch.as_tensor(c.phi).cuda()
+
+    def side(alpha):
+        s.assemble(alpha, phi0, c.rho_w, c.rho_a, c.g, c.ref_cell)
+        ex = {k: v.cpu().numpy() for k, v in s.export_system().items()}
+        dr = (ex["b"] - ex0["b"]) - apply(ex["diag"] - ex0["diag"], ex["gamma"] - ex0["gamma"], p0)
+        _, _, mu, inf = s.adjoint(p, wt, mode="fp64", rtol=1e-10)
+        assert inf.status == 0
+        return mu.cpu().numpy(), dr
+
+    fc = oracle.faces(c)
+    ifc = np.nonzero(fc.kind >= 2)[0]
+    cand = np.unique(np.concatenate([c.owner[ifc], c.neighbour[ifc]]))
+    cand = cand[(np.abs(c.alpha[cand] - 0.5) > 1e-3) & (w[cand] > 0)]
+    rng = np.random.default_rng(2005)
+    eps = 1e-6
+    worst = 0.0
+    for i in rng.choice(cand, min(16, cand.size), replace=False):
+        e = torch.zeros(c.n, dtype=torch.float64, device="cuda")
+        e[int(i)] = eps
+        mu_p, dr_p = side(alpha0 + e)
+        mu_m, dr_m = side(alpha0 - e)
+        dL = (mu_p - mu_m) @ r0 + mu_p @ dr_p - mu_m @ dr_m
+        fd = dL / (2 * eps)
+        rel = abs(fd - dalpha[i]) / max(abs(dalpha[i]), 1e-3 * np.abs(dalpha).max())
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (i, fd, dalpha[i], rel)
+    print(f"dL/dalpha vs eps=1e-6 central differences, worst relative deviation {worst:.2e}")
