@@ -34,6 +34,7 @@ struct gfm_ctx {
     double *b = nullptr, *diag = nullptr, *dinv = nullptr, *x64 = nullptr, *r64 = nullptr;
     double *p64 = nullptr, *q64 = nullptr, *rhs = nullptr, *tmp_user = nullptr, *tmp_user2 = nullptr;
     float2 *UP0 = nullptr, *UP1 = nullptr;
+    float *P32 = nullptr;
     float *R32 = nullptr, *S32 = nullptr, *E = nullptr, *dinv32 = nullptr;
     // two-level preconditioner (coarse space of connected one-phase regions)
     int32_t *cc_parent = nullptr, *cc_size = nullptr, *cc_cand = nullptr, *cc_counters = nullptr;
@@ -105,7 +106,8 @@ void free_all(gfm_ctx *h)
     void *ptrs[] = {h->owner, h->neighbour, h->Sf, h->C, h->perm, h->iperm, h->slice_ptr, h->col, h->face,
                     h->val64, h->val32, h->lambda, h->gamma, h->jump, h->sigma, h->phi, h->dl_dlam, h->kind,
                     h->alpha, h->b, h->diag, h->dinv, h->x64, h->r64, h->p64, h->q64, h->rhs, h->tmp_user,
-                    h->tmp_user2, h->UP0, h->UP1, h->R32, h->S32, h->E, h->dinv32, h->stage_alpha, h->stage_phi, h->stage_p, h->prm, h->bar,
+                    h->tmp_user2, h->UP0, h->UP1, h->P32, h->R32, h->S32, h->E, h->dinv32, h->stage_alpha,
+                    h->stage_phi, h->stage_p, h->prm, h->bar,
                     h->err, h->partials, h->dinfo, h->cc_parent, h->cc_size, h->cc_cand, h->cc_counters,
                     h->comp, h->cross, h->coarse, h->ftank, h->stank, h->tncell, h->tphys, h->tprm, h->cta,
                     h->tank_cta, h->binfos};
@@ -256,6 +258,7 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
     a.q64 = h->q64;
     a.UP0 = h->UP0;
     a.UP1 = h->UP1;
+    a.P32 = h->P32;
     a.R32 = h->R32;
     a.S32 = h->S32;
     a.E = h->E;
@@ -379,7 +382,7 @@ gfm_status alloc_upload(gfm_ctx *h, cudaStream_t s)
     A(val64, ns); A(val32, ns);
     A(lambda, F); A(gamma, F); A(jump, F); A(sigma, F); A(phi, F); A(dl_dlam, F); A(kind, F);
     A(alpha, n); A(b, np); A(diag, np); A(dinv, np); A(x64, np); A(r64, np); A(p64, np); A(q64, np);
-    A(rhs, np); A(tmp_user, n); A(tmp_user2, n); A(UP0, np); A(UP1, np); A(R32, np); A(S32, np); A(E, np);
+    A(rhs, np); A(tmp_user, n); A(tmp_user2, n); A(UP0, np); A(UP1, np); A(P32, np); A(R32, np); A(S32, np); A(E, np);
     A(dinv32, np);
     A(stage_alpha, n); A(stage_phi, F); A(stage_p, n);
     A(prm, 1); A(bar, 1); A(err, 1); A(partials, 2 * (size_t)h->max_grid * 12); A(dinfo, 1);

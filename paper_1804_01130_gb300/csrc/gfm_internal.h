@@ -85,6 +85,7 @@ struct SolveArgs {
     double *p64, *q64;     // FP64-mode CG vectors
     float2 *UP0, *UP1;     // MIXED: (u, p) pairs, double-buffered (gathered)
     float *R32, *S32, *E;  // MIXED: scaled residual, s = A p, FP32 correction
+    float *P32;            // MIXED: this iteration's direction p (written whole, read by the update pass)
     const float *dinv32;   // MIXED: 1 / (float)diag
     const int32_t *iperm;  // [n] internal -> caller index
     double *p_user;        // caller-order x0 in / solution out

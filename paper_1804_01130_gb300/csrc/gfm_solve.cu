@@ -913,6 +913,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     float *__restrict__ E = a.E;
     float *__restrict__ R32 = a.R32;
     float *__restrict__ S32 = a.S32;
+    float *__restrict__ P32 = a.P32;
     const float *__restrict__ dinv = a.dinv32;
     const int8_t *__restrict__ comp = a.comp;
 
@@ -1015,7 +1016,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (sb + u * R.nw < R.s1 && ii[u] < n) {
-                    nxt[ii[u]].y = pn[u];
+                    P32[ii[u]] = pn[u];
                     S32[ii[u]] = si[u];
                     ff_add(accA[0], pn[u] * si[u]);
                     if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
@@ -1086,7 +1087,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             for (int u = 0; u < UB; ++u) {
                 ii[u] = (sb + u * R.nw) * kSlice + R.lane;
                 act[u] = sb + u * R.nw < R.s1 && ii[u] < n;
-                pi[u] = act[u] ? nxt[ii[u]].y : 0.f;
+                pi[u] = act[u] ? P32[ii[u]] : 0.f;
                 si[u] = act[u] ? S32[ii[u]] : 0.f;
                 ri[u] = act[u] ? R32[ii[u]] : 0.f;
                 ei[u] = act[u] ? E[ii[u]] : 0.f;
@@ -1101,7 +1102,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                     R32[ii[u]] = rn;
                     float un = rn * di[u];
                     if (cm[u] >= 0) un += sh.c32[cm[u]];
-                    nxt[ii[u]].x = un;
+                    nxt[ii[u]] = make_float2(un, pi[u]);
                     ff_add(accB[0], rn * un);
                     ff_add(accB[1], rn * rn);
                 }
@@ -1300,6 +1301,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     float *__restrict__ E = a.E;
     float *__restrict__ R32 = a.R32;
     float *__restrict__ S32 = a.S32;
+    float *__restrict__ P32 = a.P32;
     const float *__restrict__ dinv = a.dinv32;
     const double rtol2 = a.rtol * a.rtol;
     const int cap_updates = a.max_refine + 1 + (int)(2.0 * log10(1.0 / a.rtol));
@@ -1409,7 +1411,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (sb + u * R.nw < R.s1 && ii[u] < cend) {
-                        nxt[ii[u]].y = pn[u];
+                        P32[ii[u]] = pn[u];
                         S32[ii[u]] = si[u];
                         ff_add(accA[0], pn[u] * si[u]);
                     }
@@ -1441,7 +1443,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                 for (int u = 0; u < UB; ++u) {
                     ii[u] = (sb + u * R.nw) * kSlice + R.lane;
                     act[u] = sb + u * R.nw < R.s1 && ii[u] < cend;
-                    pi[u] = act[u] ? nxt[ii[u]].y : 0.f;
+                    pi[u] = act[u] ? P32[ii[u]] : 0.f;
                     si[u] = act[u] ? S32[ii[u]] : 0.f;
                     ri[u] = act[u] ? R32[ii[u]] : 0.f;
                     ei[u] = act[u] ? E[ii[u]] : 0.f;
@@ -1454,7 +1456,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                         const float rn = fmaf(-al, si[u], ri[u]);
                         R32[ii[u]] = rn;
                         const float un = rn * di[u];
-                        nxt[ii[u]].x = un;
+                        nxt[ii[u]] = make_float2(un, pi[u]);
                         ff_add(accB[0], rn * un);
                         ff_add(accB[1], rn * rn);
                     }
