@@ -152,6 +152,7 @@ gfm_status check_opts(gfm_ctx *h, const gfm_solve_opts *o)
 // slots (neighbour + coefficient) as fit next to the other CTAs of its SM.
 struct LaunchPlan {
     int grid = 0, threads = 0, cache_cap = 0, meta_slots = 0;
+    int n_stages = 0, stage_slices = 0, stage_cap = 0;  // streamed tables (MIXED), 0 = not streamed
     size_t dyn = 0;
 };
 
@@ -198,7 +199,28 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     cap = std::min<long long>(cap, max_slots);
     cap &= ~3LL;
     if (meta_bytes > budget) return fail(h, GFM_ERR_ARG, "mesh too large for this launch shape");
-    const size_t dyn = (size_t)(meta_bytes + cap * slot_bytes);
+    // Tables that do not fit: the mixed operator pass streams them through a
+    // ring of 3 (else 2) stages, each a whole number of pass rounds (a round
+    // = the slices the CTA's warps take at once: 4 per warp for rows of <= 4
+    // faces, else 2).
+    int n_stages = 0, stage_slices = 0, stage_cap = 0;
+    if (mode == gfm::Mode::MIXED && !h->batched && cap < max_slots) {
+        const int maxw = std::max(1, h->ht.max_width);
+        const int unit = (maxw <= 4 ? 4 : 2) * (t / 32);
+        const long long per_unit = (long long)unit * 32 * maxw * 8;
+        const long long need = (max_nsl + unit - 1) / unit;
+        for (int S = 3; S >= 2 && n_stages == 0; --S) {
+            const long long m = std::min<long long>((budget - meta_bytes) / (S * per_unit), need);
+            if (m >= 1) {
+                n_stages = S;
+                stage_slices = (int)(unit * m);
+                stage_cap = stage_slices * 32 * maxw;
+            }
+        }
+        if (n_stages) cap = 0;
+    }
+    const size_t dyn = (size_t)(meta_bytes + (n_stages ? (long long)n_stages * stage_cap * 8 : cap * slot_bytes));
+    if (n_stages) k = gfm::solver_kernel(mode, h->ht.max_width, t, true);
     GFM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int occ = 0;
     GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, t, dyn));
@@ -207,6 +229,9 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     lp->threads = t;
     lp->cache_cap = (int)cap;
     lp->meta_slots = meta_slots;
+    lp->n_stages = n_stages;
+    lp->stage_slices = stage_slices;
+    lp->stage_cap = stage_cap;
     lp->dyn = dyn;
     return GFM_OK;
 }
@@ -276,12 +301,15 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
     a.cross = h->cross;
     a.cache_cap = lp.cache_cap;
     a.meta_slots = lp.meta_slots;
+    a.n_stages = lp.n_stages;
+    a.stage_slices = lp.stage_slices;
+    a.stage_cap = lp.stage_cap;
     a.bar = h->bar;
     a.err = h->err;
     a.partials = h->partials;
     a.info = info_dev;
     gfm::BatchArgs ba{};
-    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads);
+    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads, lp.n_stages > 0);
     if (h->batched) {
         a.n_per_tank = h->tncell;
         a.prm = h->tprm;

@@ -13,6 +13,7 @@ constexpr int kSlice = 32;  // cells per sliced-ELL slice (one warp, one lane pe
 constexpr int kMaxCoarse = 8;         // coarse vectors of the two-level preconditioner
 constexpr int kMaxCandidates = 4096;  // components examined when choosing them
 constexpr int kMaxTanks = 128;        // tanks of one batched solve
+constexpr int kMaxStages = 4;         // shared-memory stages of streamed slice tables
 
 // Physics of one tank of a batch (device copy of gfm_phys, ref internal).
 struct TankPhys {
@@ -98,6 +99,10 @@ struct SolveArgs {
     const int32_t *n_per_tank;  // batched: real cells of each tank (else nullptr)
     int32_t cache_cap;     // slots of a CTA's slice tables staged in shared memory
     int32_t meta_slots;    // slice-metadata entries reserved in shared memory
+    int32_t n_stages;      // MIXED: > 0 = the operator pass streams the tables through
+                           // this many shared-memory stages (bulk async copies)
+    int32_t stage_slices;  // slices per stage (a multiple of the slices a pass round covers)
+    int32_t stage_cap;     // slots per stage
     unsigned int *bar;     // grid-barrier arrival counter (zeroed before launch)
     int *err;              // device status (zeroed before launch)
     double *partials;      // [2][grid][4] per-CTA partial sums
@@ -186,7 +191,7 @@ struct BatchArgs {
 const void *batched_kernel(int max_width);
 
 enum class Mode { FP64 = 0, MIXED = 1 };
-const void *solver_kernel(Mode m, int max_width, int threads);
+const void *solver_kernel(Mode m, int max_width, int threads, bool streamed = false);
 int solver_max_threads();
 
 }  // namespace gfm

@@ -82,6 +82,7 @@ struct Ctl {
 };
 
 struct Shared {
+    unsigned long long mbar[kMaxStages];  // completion barriers of the streamed-table stages
     float2 warp_ff[32][kMaxNR];
     double warp_d[32][kMaxNR];
     double out[kMaxNR];
@@ -93,6 +94,7 @@ struct Shared {
     double zb64[kMaxCoarse];
     double Einv[kMaxCoarse * kMaxCoarse];  // staged copy of the coarse inverse
     int flag;
+    int ring_fail;  // a streamed-table stage did not arrive within the budget
 };
 
 struct Grid {
@@ -339,6 +341,161 @@ __device__ Tab<V> stage_tables(const Sell &m, const V *gval, const Range &R, int
     t.base0 = base0;
     t.end = base0 + cap;
     return t;
+}
+
+// Streamed tables.  When a CTA's slots do not fit in shared memory, the
+// mixed operator pass streams them through a ring of shared-memory stages
+// filled by 1D bulk async copies (cp.async.bulk, completion counted in
+// bytes on one mbarrier per stage).  A stage holds the (neighbour,
+// coefficient) slots of `stage_slices` consecutive slices; while the CTA
+// works on stage r the copies of stages r+1 .. r+S-1 are in flight, so the
+// largest stream of the pass needs no registers to stay in flight.  As soon
+// as a pass ends, the first stages of the next pass are requested.  Slot
+// ranges start on 128-byte boundaries (slice bases are multiples of 32 slots)
+// and their byte counts are multiples of 128, as bulk copies require.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct Ring {
+    unsigned char *buf;       // n_stages x (col [cap] | val [cap])
+    unsigned long long *bar;  // [n_stages]
+    const int2 *meta;         // the CTA's staged slice (base, width)
+    const int32_t *gcol;
+    const float *gval;
+    int n_stages, stage_slices, cap, nsl, nr, s0, tab_end;
+    unsigned issued;  // stages requested so far (thread 0 only)
+    unsigned used;    // stages consumed so far (every thread)
+};
+
+// Stage geometry of round r (slices s0 + r*stage_slices ...).
+__device__ __forceinline__ int ring_begin(const Ring &g, int r) { return g.meta[r * g.stage_slices].x; }
+__device__ __forceinline__ int ring_end(const Ring &g, int r)
+{
+    const int e = (r + 1) * g.stage_slices;
+    return e < g.nsl ? g.meta[e].x : g.tab_end;
+}
+
+// Thread 0: request round r into the next stage of the ring.
+__device__ __forceinline__ void ring_issue(Ring &g, int r)
+{
+    const int st = (int)(g.issued % (unsigned)g.n_stages);
+    unsigned long long *bar = g.bar + st;
+    const int b = ring_begin(g, r);
+    const unsigned bytes = (unsigned)(ring_end(g, r) - b) * 4u;
+    int32_t *col = reinterpret_cast<int32_t *>(g.buf + (size_t)st * g.cap * 8);
+    float *val = reinterpret_cast<float *>(col + g.cap);
+    mbar_arrive_expect_tx(bar, 2u * bytes);
+    if (bytes != 0u) {
+        bulk_load(col, g.gcol + b, bytes, bar);
+        bulk_load(val, g.gval + b, bytes, bar);
+    }
+    ++g.issued;
+}
+
+// Thread 0: request the first stages of a pass.
+__device__ __forceinline__ void ring_prefetch(Ring &g)
+{
+    const int k = min(g.n_stages, g.nr);
+    for (int r = 0; r < k; ++r) ring_issue(g, r);
+}
+
+// Wait, bounded by `budget` ns, until stage `g.used` has landed.
+__device__ __forceinline__ bool ring_wait(const Ring &g, unsigned long long budget)
+{
+    unsigned long long *bar = g.bar + (g.used % (unsigned)g.n_stages);
+    const unsigned par = (g.used / (unsigned)g.n_stages) & 1u;
+    if (mbar_try_wait(bar, par)) return true;
+    const unsigned long long t0 = gtime();
+    while (!mbar_try_wait(bar, par))
+        if (gtime() - t0 > budget) return false;
+    return true;
+}
+
+// Thread 0, before the CTA returns: wait (bounded) for every stage still in
+// flight, so no copy lands in shared memory after the CTA has left.
+__device__ __forceinline__ void ring_drain(Ring &g, unsigned long long budget)
+{
+    for (; g.used < g.issued; ++g.used)
+        if (!ring_wait(g, budget)) return;
+}
+
+// Table view of the stage holding round r.
+struct StageTab {
+    const int2 *meta;
+    const int32_t *col;
+    const float *val;
+    int s0, begin;
+
+    __device__ __forceinline__ Row row(int s) const
+    {
+        const int2 m = meta[s - s0];
+        return Row{m.x, m.y};
+    }
+    __device__ __forceinline__ int c(int slot) const { return col[slot - begin]; }
+    __device__ __forceinline__ float v(int slot) const { return val[slot - begin]; }
+};
+
+__device__ __forceinline__ StageTab ring_stage(const Ring &g, int r)
+{
+    const int st = (int)(g.used % (unsigned)g.n_stages);
+    const int32_t *col = reinterpret_cast<const int32_t *>(g.buf + (size_t)st * g.cap * 8);
+    return StageTab{g.meta, col, reinterpret_cast<const float *>(col + g.cap), g.s0, ring_begin(g, r)};
+}
+
+// Set up the ring after stage_tables (the slice metadata is in shared
+// memory).  n_stages = 0: tables are read from the static cache / L2.
+__device__ Ring make_ring(const SolveArgs &a, const Range &R, const int2 *meta, unsigned char *dsm, Shared &sh)
+{
+    Ring g{};
+    g.n_stages = a.n_stages;
+    if (g.n_stages <= 0) return g;
+    g.buf = dsm + (size_t)a.meta_slots * sizeof(int2);
+    g.bar = sh.mbar;
+    g.meta = meta;
+    g.gcol = a.m.col;
+    g.gval = a.m.val32;
+    g.stage_slices = a.stage_slices;
+    g.cap = a.stage_cap;
+    g.s0 = R.s0;
+    g.nsl = R.s1 - R.s0;
+    g.nr = (g.nsl + g.stage_slices - 1) / g.stage_slices;
+    g.tab_end = g.nsl > 0 ? meta[g.nsl - 1].x + kSlice * meta[g.nsl - 1].y : 0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < g.n_stages; ++k) mbar_init(g.bar + k, 1u);
+        sh.ring_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    return g;
 }
 
 // (A x)_i in FP64, difference form: sum_f gamma_f (x_i - x_j) + pin x_i.
@@ -891,9 +1048,72 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
     return true;
 }
 
+// One group of the mixed operator pass: slices sb, sb + nw, ... (U of them,
+// those before s_end): p = u + beta p for the cell and, from the gathered
+// (u, p) pairs, for its neighbours; s = A p in difference form; p into P32,
+// s into S32, p.s into acc (and the pin's share of Z^T A p).
+template <int CH, int U, typename TabT>
+__device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_end, const Range &R, int n,
+                                               const float2 *cur, float *P32, float *S32, float be, int ref,
+                                               float pin32, int rc, int K, Shared &sh, FF &acc)
+{
+    int ii[U], base[U], w[U];
+    float2 v[U];
+    float pn[U], si[U];
+    int wmax = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int s = sb + u * R.nw;
+        ii[u] = s * kSlice + R.lane;
+        base[u] = 0;
+        w[u] = 0;
+        const bool act = s < s_end && ii[u] < n;
+        if (act) {
+            const Row rw = tab.row(s);
+            base[u] = rw.base;
+            w[u] = rw.w;
+        }
+        v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
+        pn[u] = fmaf(be, v[u].y, v[u].x);
+        si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+        wmax = max(wmax, w[u]);
+    }
+    for (int k0 = 0; k0 < wmax; k0 += CH) {
+        int j[U][CH];
+        float gm[U][CH];
+        float2 vj[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const bool ok = k0 + c < w[u];
+                const int slot = base[u] + (k0 + c) * kSlice + R.lane;
+                j[u][c] = ok ? tab.c(slot) : 0;
+                gm[u][c] = ok ? tab.v(slot) : 0.0f;
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (sb + u * R.nw < s_end && ii[u] < n) {
+            P32[ii[u]] = pn[u];
+            S32[ii[u]] = si[u];
+            ff_add(acc, pn[u] * si[u]);
+            if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
+        }
+    }
+}
+
 }  // namespace
 
-template <int CH>
+template <int CH, bool STREAM>
 __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 {
     constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass
@@ -904,6 +1124,14 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     const Range R = my_range(a.m.n_slices);
     stage_coarse(a.coarse, sh);
     const Tab<float> tab = stage_tables<float>(a.m, a.m.val32, R, a.cache_cap, a.meta_slots, dsm);
+    Ring ring{};
+    if constexpr (STREAM) ring = make_ring(a, R, tab.meta, dsm, sh);
+    // every early return first lets the stages still in flight land
+    auto bail = [&]() {
+        if constexpr (STREAM)
+            if (threadIdx.x == 0) ring_drain(ring, a.budget_ns);
+        record_abort(a);
+    };
     const int n = a.m.n;
     const int ref = a.prm->ref;
     const float pin32 = a.prm->pin32;
@@ -930,7 +1158,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     }
     block_sum_f64<1>(sh, vb);
     double tb[1];
-    if (!grid_allreduce<1>(g, sh, vb, tb)) { record_abort(a); return; }
+    if (!grid_allreduce<1>(g, sh, vb, tb)) { bail(); return; }
     // thread-0 scalar state (last_upd: iteration of the last residual replacement)
     double bnorm = 1.0, gam = 0.0, gam_prev = 1.0, rho_max = 0.0, best_rel2 = 0.0, rho_stop = 0.0;
     int stall = 0, last_upd = 0;
@@ -951,7 +1179,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     float2 *cur = a.UP0, *nxt = a.UP1;  // cur holds (u, p_old) for the next pass A
     int iters = 0, updates = 0, status = GFM_OK;
     double t[3];
-    if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, false, true, t)) { record_abort(a); return; }
+    if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, false, true, t)) { bail(); return; }
     ++updates;
     if (threadIdx.x == 0) {
         best_rel2 = t[0] / (bnorm * bnorm);
@@ -962,66 +1190,40 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     }
     __syncthreads();
     int action = sh.ctl.action;
+    if constexpr (STREAM)
+        if (threadIdx.x == 0) ring_prefetch(ring);
     while (action != kConverged) {
         const float be = sh.ctl.be;
         zero_bins(sh);
         __syncthreads();
         // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s
         FF accA[1] = {{0.f, 0.f}};
-        for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw) {
-            int ii[U], base[U], w[U];
-            float2 v[U];
-            float pn[U], si[U];
-            int wmax = 0;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int s = sb + u * R.nw;
-                ii[u] = s * kSlice + R.lane;
-                base[u] = 0;
-                w[u] = 0;
-                const bool act = s < R.s1 && ii[u] < n;
-                if (act) {
-                    const Row rw = tab.row(s);
-                    base[u] = rw.base;
-                    w[u] = rw.w;
+        if constexpr (STREAM) {
+            for (int r = 0; r < ring.nr; ++r) {
+                if (ring_wait(ring, a.budget_ns)) {
+                    const int sr0 = R.s0 + r * ring.stage_slices;
+                    const int sr1 = min(R.s1, sr0 + ring.stage_slices);
+                    const StageTab st = ring_stage(ring, r);
+                    for (int sb = sr0 + R.warp; sb < sr1; sb += U * R.nw)
+                        mixed_op_group<CH, U>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
+                } else {
+                    sh.ring_fail = 1;
                 }
-                v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
-                pn[u] = fmaf(be, v[u].y, v[u].x);
-                si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
-                wmax = max(wmax, w[u]);
+                ++ring.used;
+                __syncthreads();  // stage consumed: it may be refilled
+                if (sh.ring_fail) break;
+                if (threadIdx.x == 0 && r + ring.n_stages < ring.nr) ring_issue(ring, r + ring.n_stages);
             }
-            for (int k0 = 0; k0 < wmax; k0 += CH) {
-                int j[U][CH];
-                float gm[U][CH];
-                float2 vj[U][CH];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const bool ok = k0 + c < w[u];
-                        const int slot = base[u] + (k0 + c) * kSlice + R.lane;
-                        j[u][c] = ok ? tab.c(slot) : 0;
-                        gm[u][c] = ok ? tab.v(slot) : 0.0f;
-                    }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
+            if (sh.ring_fail) {
+                if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)GFM_ERR_TIMEOUT);
+                bail();
+                return;
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (sb + u * R.nw < R.s1 && ii[u] < n) {
-                    P32[ii[u]] = pn[u];
-                    S32[ii[u]] = si[u];
-                    ff_add(accA[0], pn[u] * si[u]);
-                    if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
-                }
-            }
+            // the next pass's first stages load during the rest of the iteration
+            if (threadIdx.x == 0) ring_prefetch(ring);
+        } else {
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
+                mixed_op_group<CH, U>(tab, sb, R.s1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
         }
         if (K > 0) {
             // Z^T (A p) from the faces between coarse regions (+ the pin)
@@ -1042,10 +1244,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             double b9[1 + kMaxCoarse];
             b9[0] = blkA[0];
             for (int k = 0; k < kMaxCoarse; ++k) b9[1 + k] = (double)sh.zb32[k];
-            if (!grid_allreduce<1 + kMaxCoarse>(g, sh, b9, tA, 1 + K)) { record_abort(a); return; }
+            if (!grid_allreduce<1 + kMaxCoarse>(g, sh, b9, tA, 1 + K)) { bail(); return; }
         } else {
             double o1[1];
-            if (!grid_allreduce<1>(g, sh, blkA, o1)) { record_abort(a); return; }
+            if (!grid_allreduce<1>(g, sh, blkA, o1)) { bail(); return; }
             tA[0] = o1[0];
         }
         if (threadIdx.x == 0) {
@@ -1060,7 +1262,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
         __syncthreads();
         if (sh.ctl.action == kRestart) {
             // breakdown of the FP32 recurrence: restart from the true residual
-            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, true, t)) { record_abort(a); return; }
+            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, true, t)) { bail(); return; }
             ++updates;
             if (threadIdx.x == 0) {
                 const double rel2 = t[0] / (bnorm * bnorm);
@@ -1110,7 +1312,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
         }
         double blkB[2], tB[2];
         block_sum_ff<2>(sh, accB, blkB);
-        if (!grid_allreduce<2>(g, sh, blkB, tB)) { record_abort(a); return; }
+        if (!grid_allreduce<2>(g, sh, blkB, tB)) { bail(); return; }
         ++iters;
         { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
         if (threadIdx.x == 0) {
@@ -1136,7 +1338,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
         if (action == kUpdate || action == kNotConverged) {
             // fold e into x (FP64) and replace r by the true residual; the
             // direction p is kept
-            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, false, t)) { record_abort(a); return; }
+            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, false, t)) { bail(); return; }
             ++updates;
             if (threadIdx.x == 0) {
                 const double rel2 = t[0] / (bnorm * bnorm);
@@ -1160,6 +1362,8 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             if (action == kNotConverged) { status = GFM_ERR_NOT_CONVERGED; break; }
         }
     }
+    if constexpr (STREAM)
+        if (threadIdx.x == 0) ring_drain(ring, a.budget_ns);
     finish<CH>(a, g, sh, R, iters, updates, status, bnorm);
 }
 
@@ -1591,12 +1795,18 @@ const void *batched_kernel(int max_width)
     return max_width <= 4 ? (const void *)k_solve_batched<4> : (const void *)k_solve_batched<8>;
 }
 
-// Instantiations by faces per row chunk: 4 for 2D hex meshes, 8 otherwise.
-const void *solver_kernel(Mode m, int max_width, int threads)
+// Instantiations by faces per row chunk (4 for 2D hex meshes, 8 otherwise)
+// and, for the mixed solver, by how the operator pass reads the tables
+// (streamed through shared-memory stages, or cached / read in place).
+const void *solver_kernel(Mode m, int max_width, int threads, bool streamed)
 {
     (void)threads;
-    if (max_width <= 4) return m == Mode::FP64 ? (const void *)k_solve_fp64<4> : (const void *)k_solve_mixed<4>;
-    return m == Mode::FP64 ? (const void *)k_solve_fp64<8> : (const void *)k_solve_mixed<8>;
+    if (max_width <= 4) {
+        if (m == Mode::FP64) return (const void *)k_solve_fp64<4>;
+        return streamed ? (const void *)k_solve_mixed<4, true> : (const void *)k_solve_mixed<4, false>;
+    }
+    if (m == Mode::FP64) return (const void *)k_solve_fp64<8>;
+    return streamed ? (const void *)k_solve_mixed<8, true> : (const void *)k_solve_mixed<8, false>;
 }
 
 int solver_max_threads() { return 512; }

@@ -1,0 +1,129 @@
+"""GPU parity at the benchmark sizes, in the launch configuration bench.py
+times (default launch shape, the workloads' renumbering and tolerances):
+
+- the 1024x512 wave tank (524 288 cells): full arrays against the oracle;
+- the 256x128x128 green-water box (4.2M cells, permuted), whose tables are
+  streamed through shared-memory stages: full assembly, the true residual
+  of the solution through the oracle's own matrix, and the solution against
+  the oracle's CG;
+- the 64-tank batch (5.2M cells in one launch): per-tank assembly and true
+  residuals, and sampled tanks against the oracle's solution.
+
+Bars as in the small-case tests: assembly bit-exact, p_d within relative L2
+1e-9 (FP64) / 1e-6 (mixed) of the oracle, true residuals at the requested
+tolerance (x1.05 for the rounding of the oracle's own residual sum).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import cases
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _g():
+    import paper_1804_01130_gb300 as g
+    return g
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _true_rel(sy, p):
+    return float(np.linalg.norm(sy.b - oracle.spmv(sy, p)) / np.linalg.norm(sy.b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+
+
+def _assembled(c, renumber):
+    s = _g().GFM.from_case(c, renumber=renumber)
+    s.assemble(torch.as_tensor(c.alpha), torch.as_tensor(c.phi), c.rho_w, c.rho_a, c.g, c.ref_cell, c.ref_value)
+    return s
+
+
+def _assembly_bit_exact(s, c):
+    ex = {k: v.cpu().numpy() for k, v in s.export_system().items()}
+    fc = oracle.faces(c)
+    sy = oracle.assemble(c, fc)
+    for k, ref in (("lambda", fc.lam), ("gamma", fc.gamma), ("jump", fc.jump), ("diag", sy.diag), ("b", sy.b)):
+        assert np.array_equal(ex[k], ref), k
+    return sy
+
+
+def test_tank2d_1024x512_full_size():
+    c = cases.make_case(2)
+    s = _assembled(c, renumber=1)
+    sy = _assembly_bit_exact(s, c)
+    p_ref, it, rel, st = oracle.pcg(sy, rtol=1e-13)
+    assert st == 0 and rel <= 1e-13
+    p64, _, i64 = s.solve(mode="fp64", rtol=1e-12)
+    assert i64.status == 0
+    assert _rel(p64.cpu().numpy(), p_ref) <= 1e-9
+    pm, _, im = s.solve(mode="mixed", rtol=1e-10, inner_rtol=1e-4, phi_corr=True)
+    assert im.status == 0
+    pmn = pm.cpu().numpy()
+    assert _true_rel(sy, pmn) <= 1.05e-10
+    assert _rel(pmn, p_ref) <= 1e-6
+
+
+def test_box3d_256x128x128_full_size():
+    c = cases.make_case(3)
+    s = _assembled(c, renumber=2)
+    sy = _assembly_bit_exact(s, c)
+    # the workload's tolerance
+    p, _, info = s.solve(mode="mixed", rtol=1e-8)
+    assert info.status == 0
+    assert _true_rel(sy, p.cpu().numpy()) <= 1.05e-8
+    # against the oracle's solution
+    p_ref, it, rel, st = oracle.pcg(sy, rtol=1e-11)
+    assert st == 0
+    pm, _, im = s.solve(mode="mixed", rtol=1e-10)
+    assert im.status == 0
+    assert _rel(pm.cpu().numpy(), p_ref) <= 1e-6
+    p64, _, i64 = s.solve(mode="fp64", rtol=1e-10)
+    assert i64.status == 0
+    assert _rel(p64.cpu().numpy(), pm.cpu().numpy()) <= 1e-6
+
+
+def test_batch64_full_size():
+    g = _g()
+    tanks = cases.batch_cases(64)
+    b = g.GFMBatch(tanks, renumber=1)
+    alpha = torch.as_tensor(np.concatenate([t.alpha for t in tanks]))
+    phi = torch.as_tensor(np.concatenate([t.phi for t in tanks]))
+    phys = [dict(rho_w=t.rho_w, rho_a=t.rho_a, g=t.g, ref_cell=t.ref_cell, ref_value=t.ref_value) for t in tanks]
+    b.assemble(alpha, phi, phys)
+    ex = {k: v.cpu().numpy() for k, v in b.export_system().items()}
+    p, _, infos = b.solve(rtol=1e-8)
+    pn = p.cpu().numpy()
+    c0 = f0 = 0
+    systems = []
+    for t, inf in zip(tanks, infos):
+        fc = oracle.faces(t)
+        sy = oracle.assemble(t, fc)
+        assert np.array_equal(ex["gamma"][f0:f0 + t.F], fc.gamma)
+        assert np.array_equal(ex["jump"][f0:f0 + t.F], fc.jump)
+        assert np.array_equal(ex["diag"][c0:c0 + t.n], sy.diag)
+        assert np.array_equal(ex["b"][c0:c0 + t.n], sy.b)
+        assert inf.status == 0, inf
+        assert _true_rel(sy, pn[c0:c0 + t.n]) <= 1.05e-8
+        systems.append((c0, sy))
+        c0 += t.n
+        f0 += t.F
+    # sampled tanks against the oracle's solution
+    p2, _, infos2 = b.solve(rtol=1e-10)
+    p2n = p2.cpu().numpy()
+    rng = np.random.default_rng(4064)
+    for k in rng.choice(len(tanks), 4, replace=False):
+        c0, sy = systems[k]
+        p_ref, _, _, st = oracle.pcg(sy, rtol=1e-11)
+        assert st == 0 and infos2[k].status == 0
+        assert _rel(p2n[c0:c0 + tanks[k].n], p_ref) <= 1e-6
