@@ -201,12 +201,12 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     if (meta_bytes > budget) return fail(h, GFM_ERR_ARG, "mesh too large for this launch shape");
     // Tables that do not fit: the mixed operator pass streams them through a
     // ring of 3 (else 2) stages, each a whole number of pass rounds (a round
-    // = the slices the CTA's warps take at once: 4 per warp for rows of <= 4
+    // = the slices the CTA's warps take at once: 4 per warp for rows of <= 6
     // faces, else 2).
     int n_stages = 0, stage_slices = 0, stage_cap = 0;
     if (mode == gfm::Mode::MIXED && !h->batched && cap < max_slots) {
         const int maxw = std::max(1, h->ht.max_width);
-        const int unit = (maxw <= 4 ? 4 : 2) * (t / 32);
+        const int unit = (maxw <= 6 ? 4 : 2) * (t / 32);
         const long long per_unit = (long long)unit * 32 * maxw * 8;
         const long long need = (max_nsl + unit - 1) / unit;
         for (int S = 3; S >= 2 && n_stages == 0; --S) {

@@ -617,16 +617,23 @@ __device__ void record_abort(const SolveArgs &a)
 
 enum Action : int { kGo = 0, kConverged = 1, kCheck = 2, kNotConverged = 3, kBreakdown = 4, kUpdate = 5, kRestart = 6 };
 
-// Thread 0: c = E^{-1} y, published in shared memory (FP64 and FP32).
-__device__ __forceinline__ void coarse_solve(const Coarse *co, int K, Shared &sh)
+// Warp 0, all lanes: c = E^{-1} y (y in shared memory), lane i forming row
+// i, published in shared memory in FP64 and FP32.  An FP64 instruction takes
+// the same pipe time on GB300 whether one lane or 32 are active, so rows in
+// parallel cost K instructions where one thread doing all of them cost K^2.
+__device__ __forceinline__ void coarse_solve_warp(int K, Shared &sh)
 {
-    (void)co;
-    for (int i = 0; i < K; ++i) {
+    __syncwarp();
+    const int i = threadIdx.x & 31;
+    if (i < K) {
         double t = 0.0;
-        for (int j = 0; j < K; ++j) t = fma(sh.Einv[i * kMaxCoarse + j], sh.y[j], t);
+#pragma unroll
+        for (int j = 0; j < kMaxCoarse; ++j)
+            if (j < K) t = fma(sh.Einv[i * kMaxCoarse + j], sh.y[j], t);
         sh.c64[i] = t;
         sh.c32[i] = (float)t;
     }
+    __syncwarp();
 }
 
 // Copy E^{-1} into shared memory once per solve.
@@ -640,6 +647,39 @@ __device__ __forceinline__ void zero_bins(Shared &sh)
     if (threadIdx.x < kMaxCoarse) {
         sh.zb32[threadIdx.x] = 0.0f;
         sh.zb64[threadIdx.x] = 0.0;
+    }
+}
+
+// Z^T (A p) over this CTA's share of the faces between coarse regions:
+// val(face) = gamma_f (p_own - p_nb) is added to the owner's region and
+// subtracted from the neighbour's.  Sums stay in registers per thread (one
+// per region), then per warp, and each warp adds them to `bins` once: the
+// interface faces mostly join the same two regions, and adding each face
+// straight into shared memory serialised on those two words.
+template <typename T, typename ValFn>
+__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, int K, T *bins, ValFn val)
+{
+    const int f0 = (int)(((long long)n_cross * blockIdx.x) / gridDim.x);
+    const int f1 = (int)(((long long)n_cross * (blockIdx.x + 1)) / gridDim.x);
+    T acc[kMaxCoarse];
+#pragma unroll
+    for (int k = 0; k < kMaxCoarse; ++k) acc[k] = T(0);
+    // taken by the CTA's last threads first, whose warps hold the fewest slices
+    const int t0 = f0 + (int)(blockDim.x - 1 - threadIdx.x);
+    for (int t = t0; t < f1; t += blockDim.x) {
+        const CrossFace cf = cross[t];
+        const T v = val(cf);
+#pragma unroll
+        for (int k = 0; k < kMaxCoarse; ++k) acc[k] += (cf.a == k ? v : T(0)) - (cf.b == k ? v : T(0));
+    }
+    if (!__any_sync(0xffffffffu, t0 < f1)) return;  // a warp without faces adds nothing
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < kMaxCoarse; ++k) {
+        T x = acc[k];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0 && k < K && x != T(0)) atomicAdd(bins + k, x);
     }
 }
 
@@ -718,14 +758,18 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
             for (int k = 0; k < kMaxCoarse; ++k) blk[3 + k] = zb[k];
             if (!grid_allreduce<3 + kMaxCoarse>(g, sh, blk, t3, 3 + K)) { record_abort(a); return; }
         }
-        if (threadIdx.x == 0) {
-            bnorm = (t3[0] > 0.0) ? sqrt(t3[0]) : 1.0;
-            rz = t3[2];
-            rr_ref = t3[1];
-            for (int k = 0; k < K; ++k) sh.y[k] = t3[3 + k];
-            coarse_solve(a.coarse, K, sh);
-            for (int k = 0; k < K; ++k) rz = fma(sh.c64[k], sh.y[k], rz);
-            sh.ctl.action = (sqrt(t3[1]) / bnorm <= a.rtol) ? kConverged : kGo;
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) {
+                bnorm = (t3[0] > 0.0) ? sqrt(t3[0]) : 1.0;
+                rz = t3[2];
+                rr_ref = t3[1];
+                for (int k = 0; k < K; ++k) sh.y[k] = t3[3 + k];
+            }
+            coarse_solve_warp(K, sh);
+            if (threadIdx.x == 0) {
+                for (int k = 0; k < K; ++k) rz = fma(sh.c64[k], sh.y[k], rz);
+                sh.ctl.action = (sqrt(t3[1]) / bnorm <= a.rtol) ? kConverged : kGo;
+            }
         }
         __syncthreads();
         if (K > 0) {
@@ -795,7 +839,9 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
             }
         }
         if (K > 0) {
-            // each CTA takes an even share of the cross faces, one per thread
+            // each CTA takes an even share of the cross faces, one per thread,
+            // added straight into shared memory: per-thread FP64 bins would
+            // cost more FP64 instructions than the few faces of a 2D tank
             const int f0 = (int)(((long long)nx * blockIdx.x) / gridDim.x);
             const int f1 = (int)(((long long)nx * (blockIdx.x + 1)) / gridDim.x);
             // taken by the CTA's last threads, whose warps hold the fewest slices
@@ -847,23 +893,30 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
         double t2[2];
         if (!grid_allreduce<2>(g, sh, v2, t2)) { record_abort(a); return; }
         ++iters;
-        if (threadIdx.x == 0) {
-            if (sqrt(t2[1]) / bnorm <= a.rtol) {
-                sh.ctl.action = kCheck;
-            } else if (K > 0 && t2[1] <= 1e-2 * rr_ref) {
-                // the residual fell a decade since Z^T r was last summed:
-                // sum it exactly again so the recurrence cannot drift
-                sh.ctl.xavg = t2[0];
-                rr_ref = t2[1];
-                sh.ctl.action = kUpdate;
-            } else {
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) {
+                if (sqrt(t2[1]) / bnorm <= a.rtol) {
+                    sh.ctl.action = kCheck;
+                } else if (K > 0 && t2[1] <= 1e-2 * rr_ref) {
+                    // the residual fell a decade since Z^T r was last summed:
+                    // sum it exactly again so the recurrence cannot drift
+                    sh.ctl.xavg = t2[0];
+                    rr_ref = t2[1];
+                    sh.ctl.action = kUpdate;
+                } else {
+                    sh.ctl.action = kGo;
+                }
+            }
+            __syncwarp();
+            if (sh.ctl.action == kGo) {
                 // z = D^{-1} r + Z E^{-1} y:  r.z = r.D^{-1}r + y.E^{-1}y
-                coarse_solve(a.coarse, K, sh);
-                double rzn = t2[0];
-                for (int k = 0; k < K; ++k) rzn = fma(sh.c64[k], sh.y[k], rzn);
-                sh.ctl.beta = rzn / rz;
-                rz = rzn;
-                sh.ctl.action = kGo;
+                coarse_solve_warp(K, sh);
+                if (threadIdx.x == 0) {
+                    double rzn = t2[0];
+                    for (int k = 0; k < K; ++k) rzn = fma(sh.c64[k], sh.y[k], rzn);
+                    sh.ctl.beta = rzn / rz;
+                    rz = rzn;
+                }
             }
         }
         __syncthreads();
@@ -884,14 +937,17 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
             block_sum_f64<kMaxCoarse>(sh, zb);
             double ty[kMaxCoarse];
             if (!grid_allreduce<kMaxCoarse>(g, sh, zb, ty, K)) { record_abort(a); return; }
-            if (threadIdx.x == 0) {
-                for (int k = 0; k < K; ++k) sh.y[k] = ty[k];
-                coarse_solve(a.coarse, K, sh);
-                double rzn = sh.ctl.xavg;
-                for (int k = 0; k < K; ++k) rzn = fma(sh.c64[k], sh.y[k], rzn);
-                sh.ctl.beta = rzn / rz;
-                rz = rzn;
-                sh.ctl.action = kGo;
+            if (threadIdx.x < 32) {
+                if (threadIdx.x == 0)
+                    for (int k = 0; k < K; ++k) sh.y[k] = ty[k];
+                coarse_solve_warp(K, sh);
+                if (threadIdx.x == 0) {
+                    double rzn = sh.ctl.xavg;
+                    for (int k = 0; k < K; ++k) rzn = fma(sh.c64[k], sh.y[k], rzn);
+                    sh.ctl.beta = rzn / rz;
+                    rz = rzn;
+                    sh.ctl.action = kGo;
+                }
             }
             __syncthreads();
             action = sh.ctl.action;
@@ -931,12 +987,16 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
                 for (int k = 0; k < kMaxCoarse; ++k) blk[2 + k] = zb[k];
                 if (!grid_allreduce<2 + kMaxCoarse>(g, sh, blk, tt, 2 + K)) { record_abort(a); return; }
             }
+            if (threadIdx.x < 32) {
+                if (threadIdx.x == 0) {
+                    ++checks;
+                    rz = tt[0];
+                    rr_ref = tt[1];
+                    for (int k = 0; k < K; ++k) sh.y[k] = tt[2 + k];
+                }
+                coarse_solve_warp(K, sh);
+            }
             if (threadIdx.x == 0) {
-                ++checks;
-                rz = tt[0];
-                rr_ref = tt[1];
-                for (int k = 0; k < K; ++k) sh.y[k] = tt[2 + k];
-                coarse_solve(a.coarse, K, sh);
                 for (int k = 0; k < K; ++k) rz = fma(sh.c64[k], sh.y[k], rz);
                 const double rel = sqrt(tt[1]) / bnorm;
                 if (rel < 0.5 * best) { best = rel; stall = 0; }
@@ -1028,9 +1088,12 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
     blk[0] = vr[0];
     for (int k = 0; k < 2 + kMaxCoarse; ++k) blk[1 + k] = ffo[k];
     if (!grid_allreduce<3 + kMaxCoarse>(g, sh, blk, tt, 3 + K)) return false;
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < K; ++k) sh.y[k] = tt[3 + k];
+        coarse_solve_warp(K, sh);
+    }
     if (threadIdx.x == 0) {
-        for (int k = 0; k < K; ++k) sh.y[k] = tt[3 + k];
-        coarse_solve(a.coarse, K, sh);
         double gam = tt[1];
         for (int k = 0; k < K; ++k) gam = fma(sh.c64[k], sh.y[k], gam);
         t[0] = tt[0];
@@ -1111,12 +1174,83 @@ __device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_en
     }
 }
 
+// The same group for tables in a shared-memory stage.  Neighbour indices
+// and coefficients are read from shared memory where they are used, so only
+// the gathered (u, p) pairs occupy registers and U rows of CH faces each
+// have all their gathers in flight at once.
+template <int CH, int U>
+__device__ __forceinline__ void mixed_op_group_staged(const StageTab &tab, int sb, int s_end, const Range &R, int n,
+                                                      const float2 *cur, float *P32, float *S32, float be, int ref,
+                                                      float pin32, int rc, int K, Shared &sh, FF &acc)
+{
+    int ii[U], base[U], w[U];
+    float2 v[U];
+    float pn[U], si[U];
+    int wmax = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int s = sb + u * R.nw;
+        ii[u] = s * kSlice + R.lane;
+        base[u] = 0;
+        w[u] = 0;
+        const bool act = s < s_end && ii[u] < n;
+        if (act) {
+            const Row rw = tab.row(s);
+            base[u] = rw.base;
+            w[u] = rw.w;
+        }
+        v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
+        wmax = max(wmax, w[u]);
+    }
+    for (int k0 = 0; k0 < wmax; k0 += CH) {
+        float2 vj[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const bool ok = k0 + c < w[u];
+                vj[u][c] = ok ? cur[tab.c(base[u] + (k0 + c) * kSlice + R.lane)] : v[u];
+            }
+        if (k0 == 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                pn[u] = fmaf(be, v[u].y, v[u].x);
+                si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float gm = (k0 + c < w[u]) ? tab.v(base[u] + (k0 + c) * kSlice + R.lane) : 0.0f;
+                si[u] = fmaf(gm, pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
+            }
+    }
+    if (wmax == 0) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            pn[u] = fmaf(be, v[u].y, v[u].x);
+            si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (sb + u * R.nw < s_end && ii[u] < n) {
+            P32[ii[u]] = pn[u];
+            S32[ii[u]] = si[u];
+            ff_add(acc, pn[u] * si[u]);
+            if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
+        }
+    }
+}
+
 }  // namespace
 
 template <int CH, bool STREAM>
 __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 {
-    constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass
+    constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass (cached tables)
+    constexpr int US = CH <= 6 ? 4 : 2;  // the same with streamed tables
     constexpr int UB = 4;       // slices in flight per warp in the update pass
     __shared__ Shared sh;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -1204,8 +1338,9 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                     const int sr0 = R.s0 + r * ring.stage_slices;
                     const int sr1 = min(R.s1, sr0 + ring.stage_slices);
                     const StageTab st = ring_stage(ring, r);
-                    for (int sb = sr0 + R.warp; sb < sr1; sb += U * R.nw)
-                        mixed_op_group<CH, U>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
+                    for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                        mixed_op_group_staged<CH, US>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh,
+                                                      accA[0]);
                 } else {
                     sh.ring_fail = 1;
                 }
@@ -1225,19 +1360,11 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
                 mixed_op_group<CH, U>(tab, sb, R.s1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
         }
-        if (K > 0) {
-            // Z^T (A p) from the faces between coarse regions (+ the pin)
-            const int f0 = (int)(((long long)nx * blockIdx.x) / gridDim.x);
-            const int f1 = (int)(((long long)nx * (blockIdx.x + 1)) / gridDim.x);
-            // taken by the CTA's last threads, whose warps hold the fewest slices
-            for (int tf = f0 + (int)(blockDim.x - 1 - threadIdx.x); tf < f1; tf += blockDim.x) {
-                const CrossFace cf = a.cross[tf];
+        if (K > 0)  // Z^T (A p) from the faces between coarse regions (the pin's share is added above)
+            cross_sums<float>(a.cross, nx, K, sh.zb32, [&](const CrossFace &cf) {
                 const float2 vo = cur[cf.o], vv = cur[cf.v];
-                const float val = cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
-                if (cf.a >= 0) atomicAdd(&sh.zb32[cf.a], val);
-                if (cf.b >= 0) atomicAdd(&sh.zb32[cf.b], -val);
-            }
-        }
+                return cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
+            });
         double blkA[1], tA[1 + kMaxCoarse];
         block_sum_ff<1>(sh, accA, blkA);
         if (K > 0) {
@@ -1250,14 +1377,23 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             if (!grid_allreduce<1>(g, sh, blkA, o1)) { bail(); return; }
             tA[0] = o1[0];
         }
-        if (threadIdx.x == 0) {
-            const double ps = tA[0];
-            const bool ok = ps > 0.0 && isfinite(ps) && gam > 0.0;
-            const double alpha = ok ? gam / ps : 0.0;
-            sh.ctl.al = (float)alpha;
-            sh.ctl.action = ok ? kGo : kRestart;
-            for (int k = 0; k < K; ++k) sh.y[k] = fma(-alpha, tA[1 + k], sh.y[k]);
-            coarse_solve(a.coarse, K, sh);
+        if (threadIdx.x < 32) {
+            // alpha in FP32 (the vectors use it in FP32; an FP64 divide by one
+            // thread costs far more), then lane k updates y_k and the warp
+            // forms the coarse correction
+            if (threadIdx.x == 0) {
+                const double ps = tA[0];
+                const bool ok = ps > 0.0 && isfinite(ps) && gam > 0.0;
+                sh.ctl.al = ok ? (float)gam / (float)ps : 0.0f;
+                sh.ctl.action = ok ? kGo : kRestart;
+            }
+            __syncwarp();
+            double zk = 0.0;  // this lane's (Z^T A p)_k, picked without indexing the array at run time
+#pragma unroll
+            for (int k = 0; k < kMaxCoarse; ++k)
+                if (k == (int)threadIdx.x) zk = tA[1 + k];
+            if ((int)threadIdx.x < K) sh.y[threadIdx.x] = fma(-(double)sh.ctl.al, zk, sh.y[threadIdx.x]);
+            coarse_solve_warp(K, sh);
         }
         __syncthreads();
         if (sh.ctl.action == kRestart) {
@@ -1329,7 +1465,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 last_upd = iters;
             }
             else {
-                sh.ctl.be = (float)(gam / gam_prev);
+                sh.ctl.be = (float)gam / (float)gam_prev;
                 sh.ctl.action = kGo;
             }
         }
@@ -1806,6 +1942,7 @@ const void *solver_kernel(Mode m, int max_width, int threads, bool streamed)
         return streamed ? (const void *)k_solve_mixed<4, true> : (const void *)k_solve_mixed<4, false>;
     }
     if (m == Mode::FP64) return (const void *)k_solve_fp64<8>;
+    if (streamed && max_width <= 6) return (const void *)k_solve_mixed<6, true>;  // hexahedra
     return streamed ? (const void *)k_solve_mixed<8, true> : (const void *)k_solve_mixed<8, false>;
 }
 
