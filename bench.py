@@ -1,31 +1,44 @@
 #!/usr/bin/env python
 """Benchmark of the GFM dynamic-pressure solve on one GB300 per rank.
 
-Workload: the 2D wave tank of 1024 x 512 hex cells (524 288 cells) on
-16 m x 4 m, water depth 2 m, four wavelengths of a ka = 0.1 second-order
-Stokes surface, rho_w = 1000, rho_a = 1, g = (0, -9.81, 0), seeded random
-divergent predicted face flux; solved to a true relative residual of 1e-10.
+Workloads (--workload, default tank2d):
+
+  tank2d   the 2D wave tank of 1024 x 512 hex cells (524 288 cells) on
+           16 m x 4 m, water depth 2 m, four wavelengths of a ka = 0.1
+           second-order Stokes surface, seeded random divergent predicted
+           face flux; true relative residual 1e-10.
+  box3d    the 3D green-water box of 256 x 128 x 128 cubes (4.2M cells) in a
+           seeded random cell order: dam-break column, Gaussian free-surface
+           bumps and falling spheres (a folded, multiply connected
+           interface); true relative residual 1e-8.
+  batch64  64 2D tanks of seeded sizes 128x64 ... 1024x256 (5.2M cells) with
+           their own wave steepness and wavelength count, solved together by
+           ONE persistent launch replayed from a CUDA graph; 1e-8 per tank.
+
+All use rho_w = 1000, rho_a = 1, g = (0, -9.81, 0), one pinned cell per mesh.
 
 A step = one pass of the hot path on device-resident inputs: assemble the
 GFM system (interface fraction, face coefficients, jump source, cell sums),
 solve it with the mixed-precision persistent solver (FP32 inner PCG inside
-FP64 refinement), and compute the corrected face flux.  The L2 is flushed
-(a 512 MiB write) before every step.
+FP64 reliable updates, two-level preconditioner on single meshes), and, on
+single meshes, compute the corrected face flux.  The L2 is flushed (a 512
+MiB write) before every step.
 
-Metric: cell-iterations per second (cells x CG iterations / step time).
-Also reported: the plain FP64 GPU solve of the same system to the same
-tolerance, both solutions' error against the CPU FP64 oracle, the roofline
-of the persistent solver kernel, the CPU oracle's own rate (cpu_baseline),
-and the end-to-end rate through the host-buffer C-ABI entry point.
+Metric: cell-iterations per second (sum over meshes of cells x CG
+iterations, divided by the step time).  Also reported: the plain FP64 GPU
+solve of the same system to the same tolerance (single meshes), the
+solutions' error against the CPU FP64 oracle, the roofline of the
+persistent solver kernel, the CPU oracle's own rate (cpu_baseline), and the
+end-to-end rate through the public API on host buffers.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfm|reference]
+                       [--workload tank2d|box3d|batch64]
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -36,12 +49,23 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "GFM pressure solve cell*iters/s (mixed FP32-inner + FP64 refinement, rtol 1e-10)"
 UNIT = "cell*iters/s"
-WORKLOAD = "tank2d_1024x512: 2D wave tank 1024x512x1 hexes on 16 m x 4 m, ka=0.1, 4 wavelengths, depth 2 m"
-RTOL = 1e-10
 INNER_RTOL = 1e-4
 FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "tank2d": dict(rtol=1e-10, desc="tank2d_1024x512: 2D wave tank 1024x512x1 hexes on 16 m x 4 m, ka=0.1, "
+                                    "4 wavelengths, depth 2 m"),
+    "box3d": dict(rtol=1e-8, desc="box3d_256x128x128: 3D green-water box 256x128x128 cubes on 4 m x 2 m x 2 m, "
+                                  "seeded random cell order, dam-break column + Gaussian bumps + falling spheres"),
+    "batch64": dict(rtol=1e-8, desc="batch64: 64 2D wave tanks of seeded sizes 128x64..1024x256 (ka 0.02-0.15, "
+                                    "1-6 wavelengths) in one persistent launch under a CUDA graph"),
+}
+
+
+def metric_name(workload: str) -> str:
+    rtol = {"tank2d": "1e-10", "box3d": "1e-8", "batch64": "1e-8"}[workload]
+    return f"GFM pressure solve cell*iters/s (mixed FP32-inner + FP64 refinement, rtol {rtol})"
 
 
 def _args():
@@ -50,6 +74,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gfm", "reference"], default="gfm")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tank2d")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
@@ -81,7 +106,11 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _traffic_record():
+def _cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def _traffic_record(workload: str):
     """DRAM bytes per launch of the solver kernel from a committed ncu summary,
     valid only while the kernel source is unchanged (else None)."""
     src = os.path.join(ROOT, "paper_1804_01130_gb300", "csrc", "gfm_solve.cu")
@@ -91,7 +120,7 @@ def _traffic_record():
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        r = rec.get("k_solve_mixed", {})
+        r = rec.get(workload, {})
         if r.get("source_sha") == sha:
             return r, sha
     except Exception:
@@ -156,29 +185,267 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def _case():
+def _bytes_model(n, F, iters, refinements):
+    """Algorithmic bytes of the mixed solver: (52 + 12 F/n) per cell-iteration
+    (FP32 vectors and operator read or written once) and (24 + 16 F/n) per
+    cell and FP64 residual replacement."""
+    return n * iters * (52 + 12 * F / n) + n * refinements * (24 + 16 * F / n)
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+class SingleMesh:
+    """tank2d / box3d: one mesh, one handle."""
+
+    def __init__(self, key: str, dev):
+        import torch
+
+        import cases
+        import paper_1804_01130_gb300 as g
+        self.key, self.dev, self.g = key, dev, g
+        self.rtol = WORKLOADS[key]["rtol"]
+        self.case = cases.make_case(2 if key == "tank2d" else 3)
+        c = self.case
+        self.n, self.F = c.n, c.F
+        self.h = g.GFM.from_case(c, renumber=1)
+        self.alpha = torch.as_tensor(c.alpha).to(dev)
+        self.phi = torch.as_tensor(c.phi).to(dev)
+        self.p = torch.empty(c.n, dtype=torch.float64, device=dev)
+        self.phys = dict(rho_w=c.rho_w, rho_a=c.rho_a, g=c.g, ref_cell=c.ref_cell, ref_value=c.ref_value)
+        self.config = {"cells": c.n, "faces": c.F, "rtol": self.rtol, "inner_rtol": INNER_RTOL, "mode": "mixed",
+                       "renumber": "rcm"}
+
+    def step(self, stream, ev=None):
+        self.h.assemble(self.alpha, self.phi, **self.phys)
+        if ev is not None:
+            ev[0].record(stream)
+        self.h.solve(mode="mixed", rtol=self.rtol, inner_rtol=INNER_RTOL, phi_corr=True, info_on_device=True,
+                     out=self.p)
+        if ev is not None:
+            ev[1].record(stream)
+
+    def launches(self) -> int:
+        return self.h.profile().launches_total
+
+    def result(self):
+        info = self.g.GFM.info_from_device(self.h._info_dev)
+        ok = info.status == 0
+        return ok, self.n * info.iters, _bytes_model(self.n, self.F, info.iters, info.refinements), \
+            {"iters_per_solve": info.iters, "refinements": info.refinements, "rel_res_l2": info.rel_res_l2}
+
+    def extras(self, flush, stream, check_oracle: bool):
+        import numpy as np
+        import torch
+        out = {}
+        p_mixed = self.p.detach().cpu().numpy()
+        self.h.assemble(self.alpha, self.phi, **self.phys)
+        fp64_ms = []
+        for i in range(2):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p64, _, info64 = self.h.solve(mode="fp64", rtol=self.rtol, phi_corr=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp64_ms.append(a.elapsed_time(b))
+        out["fp64"] = {"ms_per_solve": statistics.mean(fp64_ms), "iters": info64.iters,
+                       "cell_iters_per_s": self.n * info64.iters / (statistics.mean(fp64_ms) * 1e-3),
+                       "rel_res_l2": info64.rel_res_l2}
+        self._fp64_ms = statistics.mean(fp64_ms)
+        if check_oracle:
+            import oracle
+            oracle.set_threads(_cores())
+            sy = oracle.assemble(self.case, oracle.faces(self.case))
+            p_ref, _, _, _ = oracle.pcg(sy, rtol=1e-12 if self.key == "tank2d" else 1e-11)
+            nrm = float(np.linalg.norm(p_ref))
+            p_fp64 = p64.detach().cpu().numpy()
+            out["accuracy"] = {
+                "mixed_rel_l2_vs_oracle": float(np.linalg.norm(p_mixed - p_ref) / nrm),
+                "fp64_rel_l2_vs_oracle": float(np.linalg.norm(p_fp64 - p_ref) / nrm),
+                "mixed_true_rel_res_oracle_matrix": float(np.linalg.norm(sy.b - oracle.spmv(sy, p_mixed)) /
+                                                          np.linalg.norm(sy.b))}
+        return out
+
+    def speedup(self, kernel_ms):
+        return {"mixed_solve_ms": kernel_ms, "speedup_mixed_vs_fp64_time_to_tol": self._fp64_ms / kernel_ms}
+
+    def e2e(self, steps, flush):
+        import torch
+        c = self.case
+        a_h = torch.as_tensor(c.alpha).contiguous().pin_memory()
+        f_h = torch.as_tensor(c.phi).contiguous().pin_memory()
+        p_h = torch.zeros(c.n, dtype=torch.float64).pin_memory()
+        self.h.solve_host(a_h, f_h, p_h, mode="mixed", rtol=self.rtol, inner_rtol=INNER_RTOL, **self.phys)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = 0
+        for i in range(steps):
+            flush.fill_(float(i))
+            inf = self.h.solve_host(a_h, f_h, p_h, mode="mixed", rtol=self.rtol, inner_rtol=INNER_RTOL,
+                                    **self.phys)
+            its += inf.iters
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return {"value": c.n * its / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (c.n + c.F),
+                "d2h_bytes_per_step": 8 * c.n + 32, "ms_per_step": dt / steps * 1e3,
+                "api": "gfm_solve_host (C ABI, pinned host buffers)"}
+
+
+class Batch64:
+    """batch64: 64 tanks, one batched handle, assemble + solve captured in a CUDA graph."""
+
+    def __init__(self, key: str, dev):
+        import numpy as np
+        import torch
+
+        import cases
+        import paper_1804_01130_gb300 as g
+        self.key, self.dev, self.g = key, dev, g
+        self.rtol = WORKLOADS[key]["rtol"]
+        self.tanks = cases.batch_cases(64)
+        self.n = sum(t.n for t in self.tanks)
+        self.F = sum(t.F for t in self.tanks)
+        self.h = g.GFMBatch(self.tanks, renumber=1)
+        self.alpha = torch.as_tensor(np.concatenate([t.alpha for t in self.tanks])).to(dev)
+        self.phi = torch.as_tensor(np.concatenate([t.phi for t in self.tanks])).to(dev)
+        self.p = torch.zeros(self.n, dtype=torch.float64, device=dev)
+        self.phys = [dict(rho_w=t.rho_w, rho_a=t.rho_a, g=t.g, ref_cell=t.ref_cell, ref_value=t.ref_value)
+                     for t in self.tanks]
+        # plan + kernel attributes before capture
+        self.h.assemble(self.alpha, self.phi, self.phys)
+        self.h.solve(rtol=self.rtol, inner_rtol=INNER_RTOL)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        self.graph = torch.cuda.CUDAGraph()
+        l0 = self.h.profile().launches_total
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(self.graph, stream=s):
+                self.h.assemble(self.alpha, self.phi, self.phys)
+                self.h.solve(rtol=self.rtol, inner_rtol=INNER_RTOL, info_on_device=True, out=self.p)
+        torch.cuda.current_stream().wait_stream(s)
+        self.per_replay = self.h.profile().launches_total - l0
+        self.replays = 0
+        self.config = {"cells": self.n, "faces": self.F, "tanks": len(self.tanks), "rtol": self.rtol,
+                       "inner_rtol": INNER_RTOL, "mode": "mixed", "renumber": "rcm", "cuda_graph": True}
+
+    def step(self, stream, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        self.graph.replay()
+        self.replays += 1
+        if ev is not None:
+            ev[1].record(stream)
+
+    def launches(self) -> int:
+        return self.replays * self.per_replay
+
+    def result(self):
+        recs = self.h.infos_from_device(self.h._info_dev)
+        ok = all(r.status == 0 for r in recs)
+        ci = sum(t.n * r.iters for t, r in zip(self.tanks, recs))
+        by = sum(_bytes_model(t.n, t.F, r.iters, r.refinements) for t, r in zip(self.tanks, recs))
+        its = [r.iters for r in recs]
+        return ok, ci, by, {"iters_per_tank_min": min(its), "iters_per_tank_max": max(its),
+                            "worst_rel_res_l2": max(r.rel_res_l2 for r in recs)}
+
+    def extras(self, flush, stream, check_oracle: bool):
+        import numpy as np
+        out = {}
+        if check_oracle:
+            import oracle
+            oracle.set_threads(_cores())
+            pn = self.p.detach().cpu().numpy()
+            worst, c0 = 0.0, 0
+            for t in self.tanks:
+                sy = oracle.assemble(t, oracle.faces(t))
+                r = sy.b - oracle.spmv(sy, pn[c0:c0 + t.n])
+                worst = max(worst, float(np.linalg.norm(r) / np.linalg.norm(sy.b)))
+                c0 += t.n
+            out["accuracy"] = {"worst_tank_true_rel_res_oracle_matrix": worst}
+        return out
+
+    def speedup(self, kernel_ms):
+        return {"batched_step_ms": kernel_ms}
+
+    def e2e(self, steps, flush):
+        """Through the public API (GFMBatch) on pinned host buffers: copies in,
+        assemble, solve, the solution and the per-tank records back."""
+        import numpy as np
+        import torch
+        a_h = torch.as_tensor(np.concatenate([t.alpha for t in self.tanks])).pin_memory()
+        f_h = torch.as_tensor(np.concatenate([t.phi for t in self.tanks])).pin_memory()
+        p_h = torch.zeros(self.n, dtype=torch.float64).pin_memory()
+        a_d = torch.empty_like(self.alpha)
+        f_d = torch.empty_like(self.phi)
+
+        def once():
+            a_d.copy_(a_h, non_blocking=True)
+            f_d.copy_(f_h, non_blocking=True)
+            self.h.assemble(a_d, f_d, self.phys)
+            p, _, infos = self.h.solve(rtol=self.rtol, inner_rtol=INNER_RTOL, out=self.p)
+            p_h.copy_(p, non_blocking=True)
+            torch.cuda.synchronize()
+            return sum(t.n * r.iters for t, r in zip(self.tanks, infos))
+
+        once()
+        t0 = time.perf_counter()
+        ci = 0
+        for i in range(steps):
+            flush.fill_(float(i))
+            ci += once()
+        dt = time.perf_counter() - t0
+        return {"value": ci / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (self.n + self.F),
+                "d2h_bytes_per_step": 8 * self.n + 32 * len(self.tanks), "ms_per_step": dt / steps * 1e3,
+                "api": "GFMBatch.assemble/solve (pinned host buffers, copies in the timed region)"}
+
+
+def _make(key, dev):
+    return Batch64(key, dev) if key == "batch64" else SingleMesh(key, dev)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+def _oracle_systems(key):
+    """The oracle's assembled systems for a workload (batch64: a sample of
+    tanks), with a description."""
     import cases
-    return cases.make_case(2)
-
-
-def _cpu_baseline(case, seconds: float):
-    """The CPU oracle (as it stands) timed on the host cores: fixed-count
-    Jacobi-PCG iterations on the assembled system, sized to ~`seconds`."""
     import oracle
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    oracle.set_threads(cores)
-    fc = oracle.faces(case)
-    sy = oracle.assemble(case, fc)
+    if key == "batch64":
+        tanks = cases.batch_cases(64)
+        sample = tanks[::8]
+        return [oracle.assemble(t, oracle.faces(t)) for t in sample], f"tanks 0, 8, ..., 56 of the batch"
+    c = cases.make_case(2 if key == "tank2d" else 3)
+    return [oracle.assemble(c, oracle.faces(c))], f"the full {c.n}-cell mesh"
+
+
+def _oracle_rate(systems, seconds):
+    """Fixed-count Jacobi-PCG iterations of the oracle on each system, sized
+    so that the whole sample takes about `seconds`; returns (cell-iters, s, iters)."""
+    import oracle
+    per = 0.0
+    for sy in systems:
+        t = time.perf_counter()
+        oracle.pcg_fixed(sy, 5)
+        per += (time.perf_counter() - t) / 5
+    iters = max(5, int(seconds / max(per, 1e-9)))
     t = time.perf_counter()
-    oracle.pcg_fixed(sy, 10)
-    per = max((time.perf_counter() - t) / 10, 1e-6)
-    iters = max(10, int(seconds / per))
-    t = time.perf_counter()
-    oracle.pcg_fixed(sy, iters)
-    dt = time.perf_counter() - t
-    return {"value": case.n * iters / dt, "unit": UNIT, "cores": int(oracle.max_threads()), "kind": "oracle",
-            "sample": f"{iters} Jacobi-PCG iterations of the FP64 CSR oracle on the full {case.n}-cell tank "
-                      f"({dt:.1f} s)"}
+    ci = 0
+    for sy in systems:
+        oracle.pcg_fixed(sy, iters)
+        ci += sy.n * iters
+    return ci, time.perf_counter() - t, iters
+
+
+def _cpu_baseline(key, seconds: float):
+    import oracle
+    oracle.set_threads(_cores())
+    systems, what = _oracle_systems(key)
+    ci, dt, iters = _oracle_rate(systems, seconds)
+    return {"value": ci / dt, "unit": UNIT, "cores": int(oracle.max_threads()), "kind": "oracle",
+            "sample": f"{iters} Jacobi-PCG iterations of the FP64 CSR oracle on {what} ({dt:.1f} s)"}
 
 
 def run_reference(args, rank, world):
@@ -186,84 +453,56 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    case = _case()
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    oracle.set_threads(cores)
-    fc = oracle.faces(case)
-    sy = oracle.assemble(case, fc)
-    t = time.perf_counter()
-    oracle.pcg_fixed(sy, 10)
-    per = max((time.perf_counter() - t) / 10, 1e-6)
-    iters = max(10, int(2.0 / per))  # ~2 s per step
+    key = args.workload
+    oracle.set_threads(_cores())
+    systems, what = _oracle_systems(key)
+    per_step = 2.0  # seconds of oracle work per step
     for _ in range(args.warmup):
-        oracle.pcg_fixed(sy, iters)
-    t = time.perf_counter()
+        _oracle_rate(systems, per_step)
+    ci = dt = 0.0
     for _ in range(args.steps):
-        oracle.pcg_fixed(sy, iters)
-    dt = time.perf_counter() - t
-    value = case.n * iters * args.steps / dt
+        c, d, iters = _oracle_rate(systems, per_step)
+        ci += c
+        dt += d
+    value = ci / dt
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric_name(key), "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": case.n, "faces": case.F, "rtol": RTOL,
-                   "sample": f"{iters} PCG iterations per step"},
+        "config": {"workload": WORKLOADS[key]["desc"], "rtol": WORKLOADS[key]["rtol"],
+                   "sample": f"{iters} PCG iterations per step on {what}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(oracle.max_threads()), "kind": "oracle",
-                         "sample": f"{iters} Jacobi-PCG iterations per step of the FP64 CSR oracle, full tank"},
+                         "sample": f"{iters} Jacobi-PCG iterations per step of the FP64 CSR oracle on {what}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
 def run_gfm(args, rank, local, world):
-    import numpy as np
     import torch
-
-    import paper_1804_01130_gb300 as g
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case = _case()
-    n, F = case.n, case.F
     stream = torch.cuda.current_stream()
-
-    p_oracle = None
-    if rank == 0 and not args.no_oracle_check:
-        import oracle
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-        oracle.set_threads(cores)
-        fc = oracle.faces(case)
-        sy = oracle.assemble(case, fc)
-        p_oracle, _, _, _ = oracle.pcg(sy, rtol=1e-12)
-
-    s = g.GFM.from_case(case, renumber=1)
-    alpha = torch.as_tensor(case.alpha).to(dev)
-    phi = torch.as_tensor(case.phi).to(dev)
-    p = torch.empty(n, dtype=torch.float64, device=dev)
+    key = args.workload
+    w = _make(key, dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    phys = dict(rho_w=case.rho_w, rho_a=case.rho_a, g=case.g, ref_cell=case.ref_cell, ref_value=case.ref_value)
-
-    def step(i, ev=None):
-        flush.fill_(float(i))
-        s.assemble(alpha, phi, **phys)
-        if ev is not None:
-            ev[0].record(stream)
-        out = s.solve(mode="mixed", rtol=RTOL, inner_rtol=INNER_RTOL, phi_corr=True, info_on_device=True, out=p)
-        if ev is not None:
-            ev[1].record(stream)
-        return out
 
     for i in range(args.warmup):
-        step(i)
+        flush.fill_(float(i))
+        w.step(stream)
     torch.cuda.synchronize()
-    info = g.GFM.info_from_device(s._info_dev)
-    if info.status != 0:
-        raise SystemExit(f"mixed solve failed: {info}")
+    ok, _, _, _ = w.result()
+    if not ok:
+        raise SystemExit(f"mixed solve failed during warm-up: {w.result()}")
 
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    lt0 = s.profile().launches_total
+    l0 = w.launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(local)
@@ -271,13 +510,17 @@ def run_gfm(args, rank, local, world):
     torch.cuda.synchronize()
     t_start.record(stream)
     for i in range(args.steps):
-        step(1000 + i, evs[i])
+        flush.fill_(float(1000 + i))
+        w.step(stream, evs[i])
     t_end.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms_total = t_start.elapsed_time(t_end)
-    launches = s.profile().launches_total - lt0
-    info = g.GFM.info_from_device(s._info_dev)
+    launches = w.launches() - l0
+    ok, ci, by, per_solve = w.result()  # every step solves the same system the same way
+    if not ok:
+        raise SystemExit(f"mixed solve failed in the timed steps: {per_solve}")
+    cell_iters, bytes_alg = ci * args.steps, by
     kernel_ms = [a.elapsed_time(b) for a, b in evs]
     if world > 1:
         import torch.distributed as dist
@@ -285,81 +528,40 @@ def run_gfm(args, rank, local, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
     ms_step = ms_total / args.steps
-    iters = info.iters
-    value = world * n * iters / (ms_step * 1e-3)
+    value = world * cell_iters / (ms_total * 1e-3)
 
-    # accuracy of the mixed solution, then the plain FP64 solve of the same system
-    p_mixed = p.detach().cpu().numpy()
-    s.assemble(alpha, phi, **phys)
-    fp64_ms = []
-    for i in range(2):
-        flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        p64, _, info64 = s.solve(mode="fp64", rtol=RTOL, phi_corr=True)
-        b.record(stream)
-        torch.cuda.synchronize()
-        fp64_ms.append(a.elapsed_time(b))
-    p_fp64 = p64.detach().cpu().numpy()
-    acc = {}
-    if p_oracle is not None:
-        nrm = float(np.linalg.norm(p_oracle))
-        acc = {"mixed_rel_l2_vs_oracle": float(np.linalg.norm(p_mixed - p_oracle) / nrm),
-               "fp64_rel_l2_vs_oracle": float(np.linalg.norm(p_fp64 - p_oracle) / nrm)}
-
-    # roofline of the persistent solver kernel (the window also holds three
-    # small memsets and the corrected-flux kernel, < 0.1% of it)
+    extras = w.extras(flush, stream, rank == 0 and not args.no_oracle_check)
     kms = statistics.mean(kernel_ms)
-    alg_bytes = n * iters * (52 + 12 * F / n) + n * info.refinements * (24 + 16 * F / n)
-    achieved = alg_bytes / (kms * 1e-3) / 1e9
+    achieved = bytes_alg / (kms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    trec, sha = _traffic_record()
+    trec, sha = _traffic_record(key)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (trec["dram_bytes_per_launch"] if trec else None),
-            "kernel": "k_solve_mixed", "kernel_ms": kms, "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "bytes_model": "(52 + 12 F/n) B per cell-iteration + (24 + 16 F/n) B per cell per refinement",
-            "note": "config-2 working set (~35 MB) is L2-resident across iterations"}
+            "kernel": "k_solve_batched" if key == "batch64" else "k_solve_mixed", "kernel_ms": kms,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg,
+            "bytes_model": "(52 + 12 F/n) B per cell-iteration + (24 + 16 F/n) B per cell per FP64 replacement"}
+    if key == "tank2d":
+        roof["note"] = "the tank's FP32 working set (~35 MB) stays in L2 across iterations"
+    if key == "batch64":
+        roof["note"] = "timed window = one graph replay (assembly kernels included, <1% of it)"
 
-    # end to end through the host-buffer entry point
-    e2e = None
-    if rank == 0:
-        a_h = torch.as_tensor(case.alpha).contiguous().pin_memory()
-        f_h = torch.as_tensor(case.phi).contiguous().pin_memory()
-        p_h = torch.zeros(n, dtype=torch.float64).pin_memory()
-        s.solve_host(a_h, f_h, p_h, mode="mixed", rtol=RTOL, inner_rtol=INNER_RTOL, **phys)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its = 0
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            inf = s.solve_host(a_h, f_h, p_h, mode="mixed", rtol=RTOL, inner_rtol=INNER_RTOL, **phys)
-            its += inf.iters
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e = {"value": world * n * its / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (n + F),
-               "d2h_bytes_per_step": 8 * n + 32, "ms_per_step": dt / args.steps * 1e3}
-
+    e2e = w.e2e(args.steps, flush) if rank == 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(case, args.cpu_seconds)
+        cpu = _cpu_baseline(key, args.cpu_seconds)
 
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": n, "faces": F, "rtol": RTOL, "inner_rtol": INNER_RTOL,
-                   "mode": "mixed", "renumber": "rcm", "parallelism": f"replicas{world}",
+        "metric": metric_name(key), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[key]["desc"], **w.config, "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MiB write) before every step", "inputs": "device-resident"},
-        "iters_per_solve": iters, "refinements": info.refinements, "rel_res_l2": info.rel_res_l2,
-        "fp64": {"ms_per_solve": statistics.mean(fp64_ms), "iters": info64.iters,
-                 "cell_iters_per_s": n * info64.iters / (statistics.mean(fp64_ms) * 1e-3),
-                 "rel_res_l2": info64.rel_res_l2},
-        "mixed_solve_ms": kms,
-        "speedup_mixed_vs_fp64_time_to_tol": statistics.mean(fp64_ms) / kms,
-        "accuracy": acc,
+        **per_solve,
+        **{k: v for k, v in extras.items() if k != "accuracy"},
+        **w.speedup(kms),
+        "accuracy": extras.get("accuracy", {}),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -38,6 +38,8 @@ struct gfm_ctx {
     float *R32 = nullptr, *S32 = nullptr, *E = nullptr, *dinv32 = nullptr;
     // two-level preconditioner (coarse space of connected one-phase regions)
     int32_t *cc_parent = nullptr, *cc_size = nullptr, *cc_cand = nullptr, *cc_counters = nullptr;
+    int32_t *cc_bcount = nullptr, *cc_boff = nullptr;
+    double *cc_epart = nullptr;
     int8_t *comp = nullptr;
     gfm::CrossFace *cross = nullptr;
     gfm::Coarse *coarse = nullptr;
@@ -109,6 +111,7 @@ void free_all(gfm_ctx *h)
                     h->tmp_user2, h->UP0, h->UP1, h->P32, h->R32, h->S32, h->E, h->dinv32, h->stage_alpha,
                     h->stage_phi, h->stage_p, h->prm, h->bar,
                     h->err, h->partials, h->dinfo, h->cc_parent, h->cc_size, h->cc_cand, h->cc_counters,
+                    h->cc_bcount, h->cc_boff, h->cc_epart,
                     h->comp, h->cross, h->coarse, h->ftank, h->stank, h->tncell, h->tphys, h->tprm, h->cta,
                     h->tank_cta, h->binfos};
     for (void *p : ptrs)
@@ -416,6 +419,8 @@ gfm_status alloc_upload(gfm_ctx *h, cudaStream_t s)
     A(prm, 1); A(bar, 1); A(err, 1); A(partials, 2 * (size_t)h->max_grid * 12); A(dinfo, 1);
     h->max_cross = (int)std::min<long long>((long long)F, std::max<long long>(65536, (long long)F / 8));
     A(cc_parent, n); A(cc_size, n); A(cc_cand, gfm::kMaxCandidates); A(cc_counters, 2);
+    A(cc_bcount, (F + 255) / 256); A(cc_boff, (F + 255) / 256);
+    A(cc_epart, (size_t)gfm::kCoarseEParts * gfm::kMaxCoarse * gfm::kMaxCoarse);
     A(comp, np); A(cross, h->max_cross); A(coarse, 1);
 #undef A
     if (e != cudaSuccess)
@@ -797,6 +802,9 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
         co.csize = h->cc_size;
         co.cand = h->cc_cand;
         co.counters = h->cc_counters;
+        co.bcount = h->cc_bcount;
+        co.boff = h->cc_boff;
+        co.epart = h->cc_epart;
         co.comp = h->comp;
         co.cross = h->cross;
         co.coarse = h->coarse;

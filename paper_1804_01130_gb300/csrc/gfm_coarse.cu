@@ -63,13 +63,14 @@ __global__ void k_cc_hook(int F, const int32_t *__restrict__ owner, const int32_
     cc_union(parent, owner[f], nb[f]);
 }
 
+// Region sizes.  The roots are final here, but parent[] is not rewritten
+// with them: a concurrent find's path splitting could overwrite such a write
+// with an ancestor that is not the root.  Later kernels find the root again.
 __global__ void k_cc_count(int n, int *parent, int *csize)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int r = cc_find(parent, i);
-    parent[i] = r;
-    atomicAdd(csize + r, 1);
+    atomicAdd(csize + cc_find(parent, i), 1);
 }
 
 __global__ void k_cc_candidates(int n, const int *__restrict__ parent, const int *__restrict__ csize, int min_size,
@@ -125,55 +126,162 @@ __global__ void k_cc_select(const int *__restrict__ csize, const int *__restrict
     }
 }
 
-__global__ void k_cc_label(int n, const int *__restrict__ parent, const int32_t *__restrict__ perm,
-                           const Coarse *__restrict__ co, int8_t *comp)
+__global__ void k_cc_label(int n, int *parent, const int32_t *__restrict__ perm, const Coarse *__restrict__ co,
+                           int8_t *comp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int r = parent[i];
+    const int r = cc_find(parent, i);
     int id = -1;
     for (int k = 0; k < co->K; ++k)
         if (co->roots[k] == r) id = k;
     comp[perm[i]] = (int8_t)id;
 }
 
-// Faces joining different coarse regions: listed, and summed into
-// E = Z^T A Z (A = sum_f gamma_f (e_o - e_v)(e_o - e_v)^T + pin).
-__global__ void k_coarse_faces(int F, const int32_t *__restrict__ owner, const int32_t *__restrict__ nb,
-                               const int32_t *__restrict__ perm, const int8_t *__restrict__ comp,
-                               const double *__restrict__ gamma, Coarse *co, CrossFace *cross, int *counters,
-                               int max_cross)
+// Faces joining different coarse regions, listed in ascending face order
+// (count per block, scan of the block counts, ordered write), so the list --
+// and every sum over it -- is the same at every assembly.
+__device__ __forceinline__ bool cross_face(int f, int F, const int32_t *__restrict__ owner,
+                                           const int32_t *__restrict__ nb, const int32_t *__restrict__ perm,
+                                           const int8_t *__restrict__ comp, int K, int &o, int &v, int &a, int &b)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= F || co->K == 0) return;
-    const int o = perm[owner[f]], v = perm[nb[f]];
-    const int a = comp[o], b = comp[v];
-    if (a == b) return;
-    const double g = gamma[f];
-    const int k = atomicAdd(counters + 1, 1);
-    if (k < max_cross) {
-        CrossFace c;
-        c.o = o;
-        c.v = v;
-        c.a = (int8_t)a;
-        c.b = (int8_t)b;
-        c.g32 = (float)g;
-        c.g64 = g;
-        cross[k] = c;
+    if (f >= F || K == 0) return false;
+    o = perm[owner[f]];
+    v = perm[nb[f]];
+    a = comp[o];
+    b = comp[v];
+    return a != b;
+}
+
+__global__ void k_cross_count(int F, const int32_t *__restrict__ owner, const int32_t *__restrict__ nb,
+                              const int32_t *__restrict__ perm, const int8_t *__restrict__ comp, const Coarse *co,
+                              int *bcount)
+{
+    int o, v, a, b;
+    const bool x = cross_face(blockIdx.x * blockDim.x + threadIdx.x, F, owner, nb, perm, comp, co->K, o, v, a, b);
+    const int c = __syncthreads_count(x);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = c;
+}
+
+// One block of 1024 threads: exclusive scan of the block counts; the total
+// goes to counters[1].
+__global__ void k_cross_scan(int nblk, const int *__restrict__ bcount, int *boff, int *counters)
+{
+    __shared__ int warp_tot[32];
+    const int per = (nblk + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(nblk, (int)threadIdx.x * per), b1 = min(nblk, b0 + per);
+    int s = 0;
+    for (int q = b0; q < b1; ++q) s += bcount[q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
     }
-    if (a >= 0) atomicAdd(&co->E[a * kMaxCoarse + a], g);
-    if (b >= 0) atomicAdd(&co->E[b * kMaxCoarse + b], g);
-    if (a >= 0 && b >= 0) {
-        atomicAdd(&co->E[a * kMaxCoarse + b], -g);
-        atomicAdd(&co->E[b * kMaxCoarse + a], -g);
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int t = lane < nw ? warp_tot[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
+        }
+        warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    int run = inc - s + (warp > 0 ? warp_tot[warp - 1] : 0);
+    for (int q = b0; q < b1; ++q) {
+        boff[q] = run;
+        run += bcount[q];
+    }
+    if (threadIdx.x == blockDim.x - 1) counters[1] = run;
+}
+
+__global__ void k_cross_write(int F, const int32_t *__restrict__ owner, const int32_t *__restrict__ nb,
+                              const int32_t *__restrict__ perm, const int8_t *__restrict__ comp,
+                              const double *__restrict__ gamma, const Coarse *co, const int *__restrict__ boff,
+                              CrossFace *cross, int max_cross)
+{
+    __shared__ int wcount[32];
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    int o = 0, v = 0, a = 0, b = 0;
+    const bool x = cross_face(f, F, owner, nb, perm, comp, co->K, o, v, a, b);
+    const unsigned m = __ballot_sync(0xffffffffu, x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wcount[warp] = __popc(m);
+    __syncthreads();
+    if (!x) return;
+    int pos = boff[blockIdx.x] + __popc(m & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; ++w) pos += wcount[w];
+    if (pos >= max_cross) return;
+    const double g = gamma[f];
+    CrossFace c;
+    c.o = o;
+    c.v = v;
+    c.a = (int8_t)a;
+    c.b = (int8_t)b;
+    c.g32 = (float)g;
+    c.g64 = g;
+    cross[pos] = c;
+}
+
+// E = Z^T A Z over the cross faces (the pin is added at the end), partial
+// sums per block in a fixed order: each thread a fixed stretch of the list,
+// then warps, then the block.
+constexpr int kEBlocks = kCoarseEParts;
+constexpr int kEThreads = 256;
+
+__global__ void k_coarse_E(const CrossFace *__restrict__ cross, const int *__restrict__ counters, int max_cross,
+                           const Coarse *co, double *epart)
+{
+    __shared__ double wsum[kEThreads / 32][kMaxCoarse * kMaxCoarse];
+    const int nx = min(counters[1], max_cross);
+    const int K = co->K;
+    double acc[kMaxCoarse * kMaxCoarse];
+    for (int q = 0; q < kMaxCoarse * kMaxCoarse; ++q) acc[q] = 0.0;
+    const long long per_blk = ((long long)nx + gridDim.x - 1) / gridDim.x;
+    const int c0 = (int)min((long long)nx, per_blk * blockIdx.x);
+    const int c1 = (int)min((long long)nx, per_blk * (blockIdx.x + 1));
+    const int per_thr = (c1 - c0 + blockDim.x - 1) / blockDim.x;
+    const int t0 = min(c1, c0 + (int)threadIdx.x * per_thr), t1 = min(c1, t0 + per_thr);
+    for (int t = t0; t < t1 && K > 0; ++t) {
+        const CrossFace cf = cross[t];
+        const double g = cf.g64;
+        if (cf.a >= 0) acc[cf.a * kMaxCoarse + cf.a] += g;
+        if (cf.b >= 0) acc[cf.b * kMaxCoarse + cf.b] += g;
+        if (cf.a >= 0 && cf.b >= 0) {
+            acc[cf.a * kMaxCoarse + cf.b] -= g;
+            acc[cf.b * kMaxCoarse + cf.a] -= g;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < kMaxCoarse * kMaxCoarse; ++q) {
+        double x = acc[q];
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) wsum[warp][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxCoarse * kMaxCoarse) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += wsum[w][threadIdx.x];
+        epart[(size_t)blockIdx.x * kMaxCoarse * kMaxCoarse + threadIdx.x] = x;
     }
 }
 
-// Pin term, Cholesky inverse of E (K <= 8, one thread); K = 0 when anything
-// is off (cross-face list overflow, E not positive definite).
+// E from the block partials (fixed order, one entry per thread), pin term,
+// Cholesky inverse (thread 0, K <= 8); K = 0 when anything is off
+// (cross-face list overflow, E not positive definite).
 __global__ void k_coarse_finish(const int8_t *__restrict__ comp, int ref, const DevParams *__restrict__ prm,
-                                Coarse *co, const int *counters, int max_cross)
+                                Coarse *co, const int *counters, int max_cross, const double *__restrict__ epart)
 {
+    if (threadIdx.x < kMaxCoarse * kMaxCoarse) {
+        double x = 0.0;
+        for (int b = 0; b < kEBlocks; ++b) x += epart[(size_t)b * kMaxCoarse * kMaxCoarse + threadIdx.x];
+        co->E[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     int K = co->K;
     const int nx = counters[1];
     if (K > 0 && nx > max_cross) K = 0;
@@ -231,10 +339,15 @@ cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches)
     k_cc_candidates<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.csize, a.min_size, a.cand, a.counters);
     k_cc_select<<<1, 32, 0, s>>>(a.csize, a.cand, a.counters, a.max_k, a.ref, a.coarse);
     k_cc_label<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.perm, a.coarse, a.comp);
-    k_coarse_faces<<<blocks_for(a.F, T), T, 0, s>>>(a.F, a.owner, a.neighbour, a.perm, a.comp, a.gamma, a.coarse,
-                                                    a.cross, a.counters, a.max_cross);
-    k_coarse_finish<<<1, 1, 0, s>>>(a.comp, a.ref, a.prm, a.coarse, a.counters, a.max_cross);
-    if (launches) *launches += 8;
+    const int nblk = blocks_for(a.F, T);
+    k_cross_count<<<nblk, T, 0, s>>>(a.F, a.owner, a.neighbour, a.perm, a.comp, a.coarse, a.bcount);
+    k_cross_scan<<<1, 1024, 0, s>>>(nblk, a.bcount, a.boff, a.counters);
+    k_cross_write<<<nblk, T, 0, s>>>(a.F, a.owner, a.neighbour, a.perm, a.comp, a.gamma, a.coarse, a.boff, a.cross,
+                                     a.max_cross);
+    k_coarse_E<<<kEBlocks, kEThreads, 0, s>>>(a.cross, a.counters, a.max_cross, a.coarse, a.epart);
+    k_coarse_finish<<<1, kMaxCoarse * kMaxCoarse, 0, s>>>(a.comp, a.ref, a.prm, a.coarse, a.counters, a.max_cross,
+                                                         a.epart);
+    if (launches) *launches += 11;
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ constexpr int kMaxCoarse = 8;         // coarse vectors of the two-level precond
 constexpr int kMaxCandidates = 4096;  // components examined when choosing them
 constexpr int kMaxTanks = 128;        // tanks of one batched solve
 constexpr int kMaxStages = 4;         // shared-memory stages of streamed slice tables
+constexpr int kCoarseEParts = 128;    // blocks summing E = Z^T A Z
 
 // Physics of one tank of a batch (device copy of gfm_phys, ref internal).
 struct TankPhys {
@@ -148,6 +149,8 @@ struct CoarseArgs {
     int32_t max_k, min_size, max_cross;
     const DevParams *prm;
     int32_t *parent, *csize, *cand, *counters;  // counters[0] = candidates, [1] = cross faces
+    int32_t *bcount, *boff;  // [ceil(F / 256)] cross faces per face block, and their offsets
+    double *epart;           // [kCoarseEParts][kMaxCoarse^2] partial sums of E
     int8_t *comp;  // internal order
     CrossFace *cross;
     Coarse *coarse;

@@ -90,8 +90,12 @@ struct Shared {
     double y[kMaxCoarse];    // thread 0: Z^T r (coarse components of the residual)
     double c64[kMaxCoarse];  // coarse correction E^{-1} Z^T r, broadcast
     float c32[kMaxCoarse];
-    float zb32[kMaxCoarse];  // this CTA's Z^T (A p) in a pass (shared-memory atomics)
+    float zb32[kMaxCoarse];  // this CTA's Z^T (A p) in a pass
     double zb64[kMaxCoarse];
+    float zbw32[16][kMaxCoarse];  // the same per warp, summed in warp order
+    double zbw64[16][kMaxCoarse];
+    float zpin32;  // the pinned cell's share, when this CTA holds it
+    double zpin64;
     double Einv[kMaxCoarse * kMaxCoarse];  // staged copy of the coarse inverse
     int flag;
     int ring_fail;  // a streamed-table stage did not arrive within the budget
@@ -648,16 +652,20 @@ __device__ __forceinline__ void zero_bins(Shared &sh)
         sh.zb32[threadIdx.x] = 0.0f;
         sh.zb64[threadIdx.x] = 0.0;
     }
+    if (threadIdx.x == 0) {
+        sh.zpin32 = 0.0f;
+        sh.zpin64 = 0.0;
+    }
 }
 
 // Z^T (A p) over this CTA's share of the faces between coarse regions:
 // val(face) = gamma_f (p_own - p_nb) is added to the owner's region and
 // subtracted from the neighbour's.  Sums stay in registers per thread (one
-// per region), then per warp, and each warp adds them to `bins` once: the
-// interface faces mostly join the same two regions, and adding each face
-// straight into shared memory serialised on those two words.
+// per region), then per warp into wbins[warp], which finish_bins adds in
+// warp order: the same result at every run, and no shared-memory atomics
+// serialised on the two words of the water/air region pair.
 template <typename T, typename ValFn>
-__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, int K, T *bins, ValFn val)
+__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, T (*wbins)[kMaxCoarse], ValFn val)
 {
     const int f0 = (int)(((long long)n_cross * blockIdx.x) / gridDim.x);
     const int f1 = (int)(((long long)n_cross * (blockIdx.x + 1)) / gridDim.x);
@@ -669,18 +677,41 @@ __device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, 
     for (int t = t0; t < f1; t += blockDim.x) {
         const CrossFace cf = cross[t];
         const T v = val(cf);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: selects are cheaper than a local-memory bin
 #pragma unroll
-        for (int k = 0; k < kMaxCoarse; ++k) acc[k] += (cf.a == k ? v : T(0)) - (cf.b == k ? v : T(0));
+            for (int k = 0; k < kMaxCoarse; ++k) acc[k] += (cf.a == k ? v : T(0)) - (cf.b == k ? v : T(0));
+        } else {
+            // FP64: two adds into a (local-memory) bin instead of 16 FP64 selects and adds
+            if (cf.a >= 0) acc[cf.a] += v;
+            if (cf.b >= 0) acc[cf.b] -= v;
+        }
     }
-    if (!__any_sync(0xffffffffu, t0 < f1)) return;  // a warp without faces adds nothing
-    const int lane = threadIdx.x & 31;
+    const bool any = __any_sync(0xffffffffu, t0 < f1);  // a warp without faces adds nothing
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kMaxCoarse; ++k) {
         T x = acc[k];
+        if (any) {
 #pragma unroll
-        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (lane == 0 && k < K && x != T(0)) atomicAdd(bins + k, x);
+            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        }
+        if (lane == 0) wbins[warp][k] = any ? x : T(0);
     }
+}
+
+// Warp 0, after a CTA barrier that follows cross_sums: bins[k] = the warps'
+// sums in warp order plus the pinned cell's share.
+template <typename T>
+__device__ __forceinline__ void finish_bins(const T (*wbins)[kMaxCoarse], T pin, int rc, int K, int nw, T *bins)
+{
+    const int k = threadIdx.x & 31;
+    if (k < K) {
+        T x = (k == rc) ? pin : T(0);
+        for (int w = 0; w < nw; ++w) x += wbins[w][k];
+        bins[k] = x;
+    }
+    __syncwarp();
 }
 
 }  // namespace
@@ -834,25 +865,15 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
                 if (sb + u * R.nw < R.s1 && ii[u] < n) {
                     q[ii[u]] = acc[u];
                     v1[0] = fma(pi[u], acc[u], v1[0]);
-                    if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb64[rc], pin64 * pi[u]);  // pin term of Z^T A p
+                    if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin64 = pin64 * pi[u];  // pin term of Z^T A p
                 }
             }
         }
-        if (K > 0) {
-            // each CTA takes an even share of the cross faces, one per thread,
-            // added straight into shared memory: per-thread FP64 bins would
-            // cost more FP64 instructions than the few faces of a 2D tank
-            const int f0 = (int)(((long long)nx * blockIdx.x) / gridDim.x);
-            const int f1 = (int)(((long long)nx * (blockIdx.x + 1)) / gridDim.x);
-            // taken by the CTA's last threads, whose warps hold the fewest slices
-            for (int t = f0 + (int)(blockDim.x - 1 - threadIdx.x); t < f1; t += blockDim.x) {
-                const CrossFace cf = a.cross[t];
-                const double val = cf.g64 * (p[cf.o] - p[cf.v]);
-                if (cf.a >= 0) atomicAdd(&sh.zb64[cf.a], val);
-                if (cf.b >= 0) atomicAdd(&sh.zb64[cf.b], -val);
-            }
-        }
+        if (K > 0)  // each CTA takes an even share of the cross faces
+            cross_sums<double>(a.cross, nx, sh.zbw64,
+                               [&](const CrossFace &cf) { return cf.g64 * (p[cf.o] - p[cf.v]); });
         block_sum_f64<1>(sh, v1);
+        if (K > 0 && threadIdx.x < 32) finish_bins<double>(sh.zbw64, sh.zpin64, rc, K, R.nw, sh.zb64);
         double t1[1 + kMaxCoarse];
         {
             double blk[1 + kMaxCoarse];
@@ -1169,7 +1190,7 @@ __device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_en
             P32[ii[u]] = pn[u];
             S32[ii[u]] = si[u];
             ff_add(acc, pn[u] * si[u]);
-            if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
+            if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p
         }
     }
 }
@@ -1239,7 +1260,7 @@ __device__ __forceinline__ void mixed_op_group_staged(const StageTab &tab, int s
             P32[ii[u]] = pn[u];
             S32[ii[u]] = si[u];
             ff_add(acc, pn[u] * si[u]);
-            if (ii[u] == ref && rc >= 0 && K > 0) atomicAdd(&sh.zb32[rc], pin32 * pn[u]);  // pin term of Z^T A p
+            if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p
         }
     }
 }
@@ -1361,7 +1382,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 mixed_op_group<CH, U>(tab, sb, R.s1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
         }
         if (K > 0)  // Z^T (A p) from the faces between coarse regions (the pin's share is added above)
-            cross_sums<float>(a.cross, nx, K, sh.zb32, [&](const CrossFace &cf) {
+            cross_sums<float>(a.cross, nx, sh.zbw32, [&](const CrossFace &cf) {
                 const float2 vo = cur[cf.o], vv = cur[cf.v];
                 return cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
             });
@@ -1370,6 +1391,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
         if (K > 0) {
             double b9[1 + kMaxCoarse];
             b9[0] = blkA[0];
+            if (threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, rc, K, R.nw, sh.zb32);
             for (int k = 0; k < kMaxCoarse; ++k) b9[1 + k] = (double)sh.zb32[k];
             if (!grid_allreduce<1 + kMaxCoarse>(g, sh, b9, tA, 1 + K)) { bail(); return; }
         } else {

@@ -230,3 +230,24 @@ def test_profiling_leaves_no_stale_error():
     s2 = _setup(c, renumber=2)
     p, _, info = s2.solve(mode="mixed", rtol=1e-11)
     assert info.status == 0
+
+
+def test_reassembly_and_solve_are_bit_reproducible():
+    """Assembly (with the coarse regions, their cross-face list and E) and
+    both solves give the same bits at every repetition: no result depends on
+    the order in which atomics or CTAs happen to run."""
+    c = cases.make_case(2)
+    g = _g()
+    s = g.GFM.from_case(c, renumber=1)
+    alpha, phi = torch.as_tensor(c.alpha).cuda(), torch.as_tensor(c.phi).cuda()
+    first = {}
+    for rep in range(6):
+        s.assemble(alpha, phi, c.rho_w, c.rho_a, c.g, c.ref_cell, c.ref_value)
+        for mode in ("mixed", "fp64"):
+            p, _, info = s.solve(mode=mode, rtol=1e-10)
+            key = (mode, info.iters, info.refinements)
+            if mode not in first:
+                first[mode] = (key, p.clone())
+            else:
+                assert key == first[mode][0], (rep, key, first[mode][0])
+                assert torch.equal(p, first[mode][1]), (rep, mode)
