@@ -78,8 +78,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
-    ap.add_argument("--profile-run", choices=["tank2d", "box3d"], default=None,
-                    help="no timing: one short mixed and one short FP64 solve for a profiler")
+    ap.add_argument("--profile-run", choices=["tank2d", "box3d", "batch64"], default=None,
+                    help="no timing: one short mixed and one short FP64 solve (batch64: one batched solve) "
+                         "for a profiler")
     ap.add_argument("--profile-iters", type=int, default=300)
     return ap.parse_args()
 
@@ -183,6 +184,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job rate: every rank (replica) processed units_per_rank units
+    within the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 def _bytes_model(n, F, iters, refinements):
@@ -522,13 +540,9 @@ def run_gfm(args, rank, local, world):
         raise SystemExit(f"mixed solve failed in the timed steps: {per_solve}")
     cell_iters, bytes_alg = ci * args.steps, by
     kernel_ms = [a.elapsed_time(b) for a, b in evs]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
-    value = world * cell_iters / (ms_total * 1e-3)
+    value = job_rate(cell_iters, world, ms_total)
 
     extras = w.extras(flush, stream, rank == 0 and not args.no_oracle_check)
     kms = statistics.mean(kernel_ms)
@@ -574,10 +588,22 @@ def run_gfm(args, rank, local, world):
 def profile_run(args):
     """One short mixed and one short FP64 solve (max_iters capped), no timing:
     the program an external profiler (ncu) wraps."""
+    import numpy as np
     import torch
 
     import cases
     import paper_1804_01130_gb300 as g
+    if args.profile_run == "batch64":
+        tanks = cases.batch_cases(64)
+        b = g.GFMBatch(tanks, renumber=1)
+        b.assemble(torch.as_tensor(np.concatenate([t.alpha for t in tanks])),
+                   torch.as_tensor(np.concatenate([t.phi for t in tanks])),
+                   [dict(rho_w=t.rho_w, rho_a=t.rho_a, g=t.g, ref_cell=t.ref_cell, ref_value=t.ref_value)
+                    for t in tanks])
+        _, _, infos = b.solve(rtol=WORKLOADS["batch64"]["rtol"], max_iters=args.profile_iters, raise_on_error=False)
+        print("batched", max(i.iters for i in infos), flush=True)
+        torch.cuda.synchronize()
+        return
     case = cases.make_case(2 if args.profile_run == "tank2d" else 3)
     s = g.GFM.from_case(case, renumber=1)
     s.assemble(torch.as_tensor(case.alpha), torch.as_tensor(case.phi), case.rho_w, case.rho_a, case.g,

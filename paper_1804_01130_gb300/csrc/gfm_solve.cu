@@ -665,7 +665,8 @@ __device__ __forceinline__ void zero_bins(Shared &sh)
 // warp order: the same result at every run, and no shared-memory atomics
 // serialised on the two words of the water/air region pair.
 template <typename T, typename ValFn>
-__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, T (*wbins)[kMaxCoarse], ValFn val)
+__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, int K, T (*wbins)[kMaxCoarse],
+                                           ValFn val)
 {
     const int f0 = (int)(((long long)n_cross * blockIdx.x) / gridDim.x);
     const int f1 = (int)(((long long)n_cross * (blockIdx.x + 1)) / gridDim.x);
@@ -691,6 +692,7 @@ __device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kMaxCoarse; ++k) {
+        if (k >= K) break;  // K is the same in every thread
         T x = acc[k];
         if (any) {
 #pragma unroll
@@ -870,7 +872,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
             }
         }
         if (K > 0)  // each CTA takes an even share of the cross faces
-            cross_sums<double>(a.cross, nx, sh.zbw64,
+            cross_sums<double>(a.cross, nx, K, sh.zbw64,
                                [&](const CrossFace &cf) { return cf.g64 * (p[cf.o] - p[cf.v]); });
         block_sum_f64<1>(sh, v1);
         if (K > 0 && threadIdx.x < 32) finish_bins<double>(sh.zbw64, sh.zpin64, rc, K, R.nw, sh.zb64);
@@ -1382,7 +1384,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 mixed_op_group<CH, U>(tab, sb, R.s1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
         }
         if (K > 0)  // Z^T (A p) from the faces between coarse regions (the pin's share is added above)
-            cross_sums<float>(a.cross, nx, sh.zbw32, [&](const CrossFace &cf) {
+            cross_sums<float>(a.cross, nx, K, sh.zbw32, [&](const CrossFace &cf) {
                 const float2 vo = cur[cf.o], vv = cur[cf.v];
                 return cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
             });
