@@ -1137,74 +1137,14 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
 // One group of the mixed operator pass: slices sb, sb + nw, ... (U of them,
 // those before s_end): p = u + beta p for the cell and, from the gathered
 // (u, p) pairs, for its neighbours; s = A p in difference form; p into P32,
-// s into S32, p.s into acc (and the pin's share of Z^T A p).
+// s into S32, p.s into acc (and the pin's share of Z^T A p).  The tables are
+// in shared memory (cached or a streamed stage): neighbour indices and
+// coefficients are read where they are used, so only the gathered pairs
+// occupy registers and all U x CH gathers of a chunk are in flight at once.
 template <int CH, int U, typename TabT>
 __device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_end, const Range &R, int n,
                                                const float2 *cur, float *P32, float *S32, float be, int ref,
                                                float pin32, int rc, int K, Shared &sh, FF &acc)
-{
-    int ii[U], base[U], w[U];
-    float2 v[U];
-    float pn[U], si[U];
-    int wmax = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int s = sb + u * R.nw;
-        ii[u] = s * kSlice + R.lane;
-        base[u] = 0;
-        w[u] = 0;
-        const bool act = s < s_end && ii[u] < n;
-        if (act) {
-            const Row rw = tab.row(s);
-            base[u] = rw.base;
-            w[u] = rw.w;
-        }
-        v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
-        pn[u] = fmaf(be, v[u].y, v[u].x);
-        si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
-        wmax = max(wmax, w[u]);
-    }
-    for (int k0 = 0; k0 < wmax; k0 += CH) {
-        int j[U][CH];
-        float gm[U][CH];
-        float2 vj[U][CH];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const bool ok = k0 + c < w[u];
-                const int slot = base[u] + (k0 + c) * kSlice + R.lane;
-                j[u][c] = ok ? tab.c(slot) : 0;
-                gm[u][c] = ok ? tab.v(slot) : 0.0f;
-            }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < CH; ++c) si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        if (sb + u * R.nw < s_end && ii[u] < n) {
-            P32[ii[u]] = pn[u];
-            S32[ii[u]] = si[u];
-            ff_add(acc, pn[u] * si[u]);
-            if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p
-        }
-    }
-}
-
-// The same group for tables in a shared-memory stage.  Neighbour indices
-// and coefficients are read from shared memory where they are used, so only
-// the gathered (u, p) pairs occupy registers and U rows of CH faces each
-// have all their gathers in flight at once.
-template <int CH, int U>
-__device__ __forceinline__ void mixed_op_group_staged(const StageTab &tab, int sb, int s_end, const Range &R, int n,
-                                                      const float2 *cur, float *P32, float *S32, float be, int ref,
-                                                      float pin32, int rc, int K, Shared &sh, FF &acc)
 {
     int ii[U], base[U], w[U];
     float2 v[U];
@@ -1362,8 +1302,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                     const int sr1 = min(R.s1, sr0 + ring.stage_slices);
                     const StageTab st = ring_stage(ring, r);
                     for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
-                        mixed_op_group_staged<CH, US>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh,
-                                                      accA[0]);
+                        mixed_op_group<CH, US>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
                 } else {
                     sh.ring_fail = 1;
                 }
