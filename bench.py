@@ -231,8 +231,11 @@ class SingleMesh:
         self.phi = torch.as_tensor(c.phi).to(dev)
         self.p = torch.empty(c.n, dtype=torch.float64, device=dev)
         self.phys = dict(rho_w=c.rho_w, rho_a=c.rho_a, g=c.g, ref_cell=c.ref_cell, ref_value=c.ref_value)
+        # launch shape picked by the library's autotuner on this system
+        self.h.assemble(self.alpha, self.phi, **self.phys)
+        thr, per_sm, _ = self.h.autotune(mode="mixed", rtol=self.rtol, inner_rtol=INNER_RTOL, trials=2)
         self.config = {"cells": c.n, "faces": c.F, "rtol": self.rtol, "inner_rtol": INNER_RTOL, "mode": "mixed",
-                       "renumber": "rcm"}
+                       "renumber": "rcm", "launch": {"threads": thr, "ctas_per_sm": per_sm, "autotuned": True}}
 
     def step(self, stream, ev=None):
         self.h.assemble(self.alpha, self.phi, **self.phys)
@@ -330,8 +333,10 @@ class Batch64:
         self.p = torch.zeros(self.n, dtype=torch.float64, device=dev)
         self.phys = [dict(rho_w=t.rho_w, rho_a=t.rho_a, g=t.g, ref_cell=t.ref_cell, ref_value=t.ref_value)
                      for t in self.tanks]
-        # plan + kernel attributes before capture
+        # plan + kernel attributes before capture; the autotuner picks the
+        # launch shape and may weight the tank->CTA table by iterations
         self.h.assemble(self.alpha, self.phi, self.phys)
+        thr, per_sm, _ = self.h.autotune(rtol=self.rtol, inner_rtol=INNER_RTOL, trials=2)
         self.h.solve(rtol=self.rtol, inner_rtol=INNER_RTOL)
         torch.cuda.synchronize()
         s = torch.cuda.Stream(device=dev)
@@ -346,7 +351,8 @@ class Batch64:
         self.per_replay = self.h.profile().launches_total - l0
         self.replays = 0
         self.config = {"cells": self.n, "faces": self.F, "tanks": len(self.tanks), "rtol": self.rtol,
-                       "inner_rtol": INNER_RTOL, "mode": "mixed", "renumber": "rcm", "cuda_graph": True}
+                       "inner_rtol": INNER_RTOL, "mode": "mixed", "renumber": "rcm", "cuda_graph": True,
+                       "launch": {"threads": thr, "ctas_per_sm": per_sm, "autotuned": True}}
 
     def step(self, stream, ev=None):
         if ev is not None:
@@ -600,6 +606,7 @@ def profile_run(args):
                    torch.as_tensor(np.concatenate([t.phi for t in tanks])),
                    [dict(rho_w=t.rho_w, rho_a=t.rho_a, g=t.g, ref_cell=t.ref_cell, ref_value=t.ref_value)
                     for t in tanks])
+        b.autotune(rtol=WORKLOADS["batch64"]["rtol"], inner_rtol=INNER_RTOL, trials=1)  # the bench's launch shape
         _, _, infos = b.solve(rtol=WORKLOADS["batch64"]["rtol"], max_iters=args.profile_iters, raise_on_error=False)
         print("batched", max(i.iters for i in infos), flush=True)
         torch.cuda.synchronize()
@@ -608,6 +615,8 @@ def profile_run(args):
     s = g.GFM.from_case(case, renumber=1)
     s.assemble(torch.as_tensor(case.alpha), torch.as_tensor(case.phi), case.rho_w, case.rho_a, case.g,
                case.ref_cell)
+    if args.profile_iters >= 100000:  # a full solve: the bench's autotuned launch shape
+        s.autotune(mode="mixed", rtol=WORKLOADS[args.profile_run]["rtol"], inner_rtol=INNER_RTOL, trials=1)
     for mode in ("mixed", "fp64"):
         _, _, info = s.solve(mode=mode, rtol=1e-10, max_iters=args.profile_iters, raise_on_error=False)
         print(mode, info, flush=True)

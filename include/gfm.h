@@ -302,6 +302,23 @@ gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t);
 gfm_status gfm_get_tuning(gfm_handle h, gfm_tuning *t);
 
 /*
+ * Autotuner: on the assembled system, time `trials` solves (median, CUDA
+ * events on `stream`) with opts for each launch shape of the persistent
+ * kernel ({512,1}, {256,2}, {128,4}, {384,1}, {256,1} threads x CTAs per
+ * SM, where co-resident).  For a batched handle it also tries the tank->CTA
+ * table weighted by the iterations each tank took (tanks that iterate longer
+ * get more CTAs).  The fastest shape and table are kept for later solves and
+ * returned in *chosen and *best_ms (either may be NULL).  The paper has no
+ * counterpart; tuning changes how the work is split, not what is computed.
+ * The trial solutions go to the handle's own workspace; synchronises
+ * `stream`.  Errors: GFM_ERR_STATE before gfm_assemble, GFM_ERR_ARG (bad
+ * opts, trials outside [1, 64]), GFM_ERR_NOT_CONVERGED when no shape solved
+ * the system (the previous shape is kept), GFM_ERR_CUDA.
+ */
+gfm_status gfm_autotune(gfm_handle h, const gfm_solve_opts *opts, int32_t trials, gfm_tuning *chosen, float *best_ms,
+                        gfm_stream stream);
+
+/*
  * Two-level preconditioner.  With a density ratio of 1000 the ghost-fluid
  * Laplacian (Sec. 3.1) couples each connected region of one phase to the rest
  * only through its interface faces, and Jacobi-PCG stalls for thousands of

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = (
     "gfm_default_opts", "gfm_create", "gfm_destroy", "gfm_assemble", "gfm_export_system", "gfm_solve",
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
-    "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc",
+    "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc", "gfm_autotune",
 )
 
 # largest n accepted by gfm_solve_csr_noalloc (its fixed device scratch)
@@ -132,6 +132,7 @@ def load_library(build_if_missing: bool = True):
         "gfm_set_coarse": ([P, I, I], S),
         "gfm_get_coarse": ([P, ct.POINTER(I), ct.POINTER(I), P, P], S),
         "gfm_solve_csr_noalloc": ([I, P, P, P, P, P, ct.c_double, I, I, ct.c_double, P, P], S),
+        "gfm_autotune": ([P, ct.POINTER(_Opts), I, ct.POINTER(_Tuning), ct.POINTER(ct.c_float), P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
     }
@@ -318,6 +319,16 @@ class GFM:
         t = _Tuning()
         self._check(self.lib.gfm_get_tuning(self.h, ct.byref(t)), "gfm_get_tuning")
         return t.threads, t.ctas_per_sm
+
+    def autotune(self, mode="mixed", rtol=1e-10, inner_rtol=1e-4, trials=3, timeout_ms=2000.0, stream=None):
+        """Time the launch shapes (and, batched, the iteration-weighted tank table) on the assembled
+        system and keep the fastest; returns (threads, ctas_per_sm, median ms)."""
+        o = self.make_opts(mode, rtol, inner_rtol, 1_000_000, 30, False, False, timeout_ms)
+        t = _Tuning()
+        ms = ct.c_float(0.0)
+        self._check(self.lib.gfm_autotune(self.h, ct.byref(o), int(trials), ct.byref(t), ct.byref(ms),
+                                          _stream(stream)), "gfm_autotune")
+        return t.threads, t.ctas_per_sm, float(ms.value)
 
     def set_coarse(self, max_vectors: int = 8, min_size: int = 64):
         """Coarse space of the two-level preconditioner (0 vectors = Jacobi only); next assembly on."""

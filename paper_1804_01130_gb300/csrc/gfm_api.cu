@@ -54,6 +54,7 @@ struct gfm_ctx {
     gfm::DevParams *tprm = nullptr, *tprm_h = nullptr;
     int4 *cta = nullptr;
     int2 *tank_cta = nullptr;
+    std::vector<double> bweight;  // per-tank work weights of the CTA table (empty: by slices)
     gfm_solve_info *binfos = nullptr, *binfos_h = nullptr;
     // host-buffer entry point staging
     double *stage_alpha = nullptr, *stage_phi = nullptr, *stage_p = nullptr;
@@ -182,7 +183,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
         if (h->cta_grid != grid) return fail(h, GFM_ERR_STATE, "batched CTA table out of date");
         std::vector<int32_t> cta4, tank2;
         std::string err;
-        if (!gfm::plan_batch_ctas(h->bt, grid, cta4, tank2, err)) return fail(h, GFM_ERR_ARG, err);
+        if (!gfm::plan_batch_ctas(h->bt, grid, cta4, tank2, err, h->bweight)) return fail(h, GFM_ERR_ARG, err);
         for (int b = 0; b < grid; ++b) {
             const int s0 = cta4[(size_t)b * 4 + 1], s1 = cta4[(size_t)b * 4 + 2];
             max_nsl = std::max(max_nsl, s1 - s0);
@@ -483,7 +484,7 @@ gfm_status plan_batch(gfm_ctx *h)
     const int grid = std::min(h->sm_count * h->tuning.ctas_per_sm, h->max_grid);
     std::vector<int32_t> cta4, tank2;
     std::string err;
-    if (!gfm::plan_batch_ctas(h->bt, grid, cta4, tank2, err)) return fail(h, GFM_ERR_ARG, err);
+    if (!gfm::plan_batch_ctas(h->bt, grid, cta4, tank2, err, h->bweight)) return fail(h, GFM_ERR_ARG, err);
     cudaError_t e = cudaMemcpy(h->cta, cta4.data(), sizeof(int32_t) * cta4.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->tank_cta, tank2.data(), sizeof(int32_t) * tank2.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "uploading the CTA table");
@@ -976,6 +977,98 @@ gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t)
             return fail(h, GFM_ERR_ARG, "launch shape cannot be co-resident");
         }
     }
+    return GFM_OK;
+}
+
+gfm_status gfm_autotune(gfm_handle h, const gfm_solve_opts *opts, int32_t trials, gfm_tuning *chosen, float *best_ms,
+                        gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    gfm_status st = check_opts(h, opts);
+    if (st != GFM_OK) return st;
+    if (trials < 1 || trials > 64) return fail(h, GFM_ERR_ARG, "trials must be in [1, 64]");
+    if (!h->assembled) return fail(h, GFM_ERR_STATE, "autotune before assemble");
+    if (h->batched && opts->mode != GFM_MIXED) return fail(h, GFM_ERR_ARG, "a batched handle solves in GFM_MIXED mode");
+    clear_stale_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    gfm_solve_opts o = *opts;
+    o.use_x0 = 0;
+    o.info_on_device = 1;
+    gfm_solve_info *idev = h->batched ? h->binfos : h->dinfo;
+    const int nrec = h->batched ? h->T : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GFM_CUDA(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(h, GFM_ERR_CUDA, "cudaEventCreate");
+    }
+    // median time of `trials` solves with the current shape and table; ms = 0
+    // when a solve fails (the candidate is then dropped)
+    auto time_it = [&](float &ms, std::vector<int32_t> *iters) -> gfm_status {
+        std::vector<float> t;
+        ms = 0.0f;
+        for (int k = 0; k < trials; ++k) {
+            GFM_CUDA(h, cudaEventRecord(e0, s));
+            if (gfm_solve(h, &o, h->tmp_user, nullptr, idev, stream) != GFM_OK) return GFM_OK;
+            GFM_CUDA(h, cudaEventRecord(e1, s));
+            GFM_CUDA(h, cudaEventSynchronize(e1));
+            float x = 0.0f;
+            GFM_CUDA(h, cudaEventElapsedTime(&x, e0, e1));
+            t.push_back(x);
+        }
+        std::vector<gfm_solve_info> rec((size_t)nrec);
+        GFM_CUDA(h, cudaMemcpy(rec.data(), idev, sizeof(gfm_solve_info) * nrec, cudaMemcpyDeviceToHost));
+        for (const auto &r : rec)
+            if (r.status != GFM_OK) return GFM_OK;
+        if (iters) {
+            iters->clear();
+            for (const auto &r : rec) iters->push_back(r.iters);
+        }
+        std::sort(t.begin(), t.end());
+        ms = t[t.size() / 2];
+        return GFM_OK;
+    };
+    const gfm_tuning start = h->tuning;
+    const std::vector<double> start_w = h->bweight;
+    // shapes within 512 threads' worth of registers per SM (the solvers use
+    // 128 registers a thread)
+    const gfm_tuning cands[] = {{512, 1}, {256, 2}, {128, 4}, {384, 1}, {256, 1}};
+    gfm_tuning best = start;
+    std::vector<double> best_w = start_w;
+    float best_t = 0.0f;
+    std::vector<int32_t> best_iters;
+    for (const gfm_tuning &c : cands) {
+        if (gfm_set_tuning(h, &c) != GFM_OK) continue;
+        float ms = 0.0f;
+        std::vector<int32_t> it;
+        st = time_it(ms, &it);
+        if (st != GFM_OK) break;
+        if (ms > 0.0f && (best_t == 0.0f || ms < best_t)) {
+            best_t = ms;
+            best = c;
+            best_iters = it;
+        }
+    }
+    if (st == GFM_OK && h->batched && best_t > 0.0f && gfm_set_tuning(h, &best) == GFM_OK) {
+        // the tank table weighted by the iterations each tank took
+        h->bweight.assign(best_iters.begin(), best_iters.end());
+        float ms = 0.0f;
+        if (plan_batch(h) == GFM_OK) st = time_it(ms, nullptr);
+        if (st == GFM_OK && ms > 0.0f && ms < best_t) {
+            best_t = ms;
+            best_w = h->bweight;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GFM_OK) return st;
+    h->bweight = best_t > 0.0f ? best_w : start_w;
+    const gfm_tuning keep = best_t > 0.0f ? best : start;
+    st = gfm_set_tuning(h, &keep);
+    if (st != GFM_OK) return st;
+    if (best_t == 0.0f) return fail(h, GFM_ERR_NOT_CONVERGED, "no launch shape solved the system");
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
     return GFM_OK;
 }
 

@@ -312,7 +312,7 @@ bool build_batch_tables(const std::vector<TankMesh> &tanks, int renumber, HostTa
 }
 
 bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4, std::vector<int32_t> &tank2,
-                     std::string &err)
+                     std::string &err, const std::vector<double> &weight)
 {
     const int T = bt.T;
     if (grid < T) {
@@ -320,14 +320,37 @@ bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4
               std::to_string(grid) + ")";
         return false;
     }
+    if (!weight.empty() && weight.size() != (size_t)T) {
+        err = "one weight per tank expected";
+        return false;
+    }
     std::vector<long long> sl((size_t)T);
     for (int k = 0; k < T; ++k) sl[(size_t)k] = (bt.ioff[(size_t)k + 1] - bt.ioff[(size_t)k]) / kSliceH;
     std::vector<int> g((size_t)T, 1);
-    for (int extra = grid - T; extra > 0; --extra) {
-        int best = 0;
-        for (int k = 1; k < T; ++k)  // load per CTA, compared exactly: sl_k / g_k > sl_b / g_b
-            if (sl[(size_t)k] * g[(size_t)best] > sl[(size_t)best] * g[(size_t)k]) best = k;
-        g[(size_t)best] += 1;
+    if (weight.empty()) {
+        for (int extra = grid - T; extra > 0; --extra) {
+            int best = 0;
+            for (int k = 1; k < T; ++k)  // load per CTA, compared exactly: sl_k / g_k > sl_b / g_b
+                if (sl[(size_t)k] * g[(size_t)best] > sl[(size_t)best] * g[(size_t)k]) best = k;
+            g[(size_t)best] += 1;
+        }
+    } else {
+        // work = slices x weight (e.g. the tank's last iteration count); a
+        // tank never gets more CTAs than slices
+        for (int extra = grid - T; extra > 0; --extra) {
+            int best = -1;
+            double bw = -1.0;
+            for (int k = 0; k < T; ++k) {
+                if (g[(size_t)k] >= sl[(size_t)k]) continue;
+                const double w = (double)sl[(size_t)k] * std::max(weight[(size_t)k], 1e-9) / g[(size_t)k];
+                if (w > bw) {
+                    bw = w;
+                    best = k;
+                }
+            }
+            if (best < 0) break;
+            g[(size_t)best] += 1;
+        }
     }
     cta4.assign((size_t)grid * 4, 0);
     tank2.assign((size_t)T * 2, 0);

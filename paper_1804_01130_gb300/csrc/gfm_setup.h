@@ -46,11 +46,12 @@ bool build_batch_tables(const std::vector<TankMesh> &tanks, int renumber, HostTa
                         std::string &err);
 
 // CTAs of a batched persistent solve: each tank gets at least one CTA and
-// the rest go, one by one, to the tank with the most slices per CTA; a tank's
-// slices are split evenly between its CTAs.  out: per CTA {tank, s0, s1, end}
-// (end = internal index one past the tank's last real cell), per tank
-// {first CTA, last CTA + 1}.
+// the rest go, one by one, to the tank with the most slices per CTA -- or,
+// with per-tank weights (e.g. the iterations each tank took last time), the
+// most slices x weight per CTA; a tank's slices are split evenly between its
+// CTAs.  out: per CTA {tank, s0, s1, end} (end = internal index one past the
+// tank's last real cell), per tank {first CTA, last CTA + 1}.
 bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4, std::vector<int32_t> &tank2,
-                     std::string &err);
+                     std::string &err, const std::vector<double> &weight = {});
 
 }  // namespace gfm

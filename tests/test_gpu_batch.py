@@ -122,3 +122,22 @@ def test_batched_rejects_bad_use():
     with pytest.raises(g.GFMError) as e:
         b.solve(mode="fp64")
     assert e.value.status == g.GFM_ERR_ARG
+
+
+def test_batched_autotune_tank_table():
+    """The autotuner may reweight the tank->CTA table by iterations; the
+    batched solve still meets every tank's tolerance and matches the oracle."""
+    tanks = _tanks()
+    g = _g()
+    b = g.GFMBatch(tanks)
+    b.assemble(_cat(tanks, "alpha"), _cat(tanks, "phi"), _phys(tanks))
+    threads, per_sm, ms = b.autotune(rtol=1e-11, trials=2)
+    assert ms > 0.0 and threads * per_sm <= 512
+    p, _, infos = b.solve(rtol=1e-11)
+    pn = p.cpu().numpy()
+    c0 = 0
+    for t, inf in zip(tanks, infos):
+        assert inf.status == 0
+        p_ref, _, _, _ = oracle.solve(t, direct=True)
+        assert np.linalg.norm(pn[c0:c0 + t.n] - p_ref) <= 1e-6 * np.linalg.norm(p_ref)
+        c0 += t.n

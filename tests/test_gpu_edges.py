@@ -251,3 +251,19 @@ def test_reassembly_and_solve_are_bit_reproducible():
             else:
                 assert key == first[mode][0], (rep, key, first[mode][0])
                 assert torch.equal(p, first[mode][1]), (rep, mode)
+
+
+def test_autotune_keeps_a_valid_shape_and_the_solution():
+    g = _g()
+    c = cases.make_case(1)
+    s = g.GFM.from_case(c)
+    s.assemble(torch.as_tensor(c.alpha), torch.as_tensor(c.phi), c.rho_w, c.rho_a, c.g, c.ref_cell, c.ref_value)
+    threads, per_sm, ms = s.autotune(mode="mixed", rtol=1e-12, trials=2)
+    assert (threads, per_sm) in {(512, 1), (256, 2), (128, 4), (384, 1), (256, 1)}
+    assert ms > 0.0
+    p_ref, _, _, _ = oracle.solve(c, direct=True, rtol=1e-14)
+    p, _, info = s.solve(mode="mixed", rtol=1e-12)
+    assert info.status == 0
+    assert np.linalg.norm(p.cpu().numpy() - p_ref) <= 1e-6 * np.linalg.norm(p_ref)
+    with pytest.raises(g.GFMError):
+        g.GFM.from_case(c).autotune()  # before assembly
