@@ -183,8 +183,9 @@ gfm_status gfm_create(const gfm_mesh *mesh, int32_t renumber, gfm_stream stream,
  * test, finished tanks drop out while the others iterate, and `info` points
  * to n_tanks records (the returned status is the last failing tank's).  The
  * launch needs at least one CTA per tank.  The adjoint and the host-buffer
- * entry point take single-mesh handles; batched tanks use the Jacobi
- * preconditioner (no coarse space).  Errors as gfm_create.
+ * entry point take single-mesh handles.  Each tank gets its own coarse space
+ * (up to its 2 largest one-phase regions, see gfm_set_coarse), so tanks
+ * iterate as a single mesh would.  Errors as gfm_create.
  */
 gfm_status gfm_create_batched(const gfm_mesh *meshes, int32_t n_tanks, int32_t renumber, gfm_stream stream,
                               gfm_handle *out);
@@ -329,8 +330,10 @@ gfm_status gfm_autotune(gfm_handle h, const gfm_solve_opts *opts, int32_t trials
  * D^{-1} + Z (Z^T A Z)^{-1} Z^T.  max_vectors = 0 gives plain Jacobi.
  * Defaults: 8 vectors, 64 cells.  Takes effect at the next gfm_assemble.
  * The coarse space needs a pin (ref_cell >= 0); unpinned systems use Jacobi.
- * gfm_get_coarse reports (host pointers, synchronises `stream`) the vectors in
- * use, the regions of at least min_size cells, and the sizes [8] of the kept ones.
+ * On a batched handle each tank keeps up to min(max_vectors, 2) regions of
+ * its own (default 2).  gfm_get_coarse reports (host pointers, synchronises
+ * `stream`) the vectors in use (summed over the tanks of a batch), the
+ * regions of at least min_size cells, and the sizes [8] of the first kept ones.
  */
 gfm_status gfm_set_coarse(gfm_handle h, int32_t max_vectors, int32_t min_size);
 gfm_status gfm_get_coarse(gfm_handle h, int32_t *n_vectors, int32_t *n_regions, int32_t *sizes, gfm_stream stream);

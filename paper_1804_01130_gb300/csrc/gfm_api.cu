@@ -54,6 +54,8 @@ struct gfm_ctx {
     gfm::DevParams *tprm = nullptr, *tprm_h = nullptr;
     int4 *cta = nullptr;
     int2 *tank_cta = nullptr;
+    int32_t *tcoff = nullptr, *tioff = nullptr;  // [T+1] caller / internal cell offsets of the tanks
+    gfm::TankCoarse *tco = nullptr;              // [T] coarse space of each tank
     std::vector<double> bweight;  // per-tank work weights of the CTA table (empty: by slices)
     gfm_solve_info *binfos = nullptr, *binfos_h = nullptr;
     // host-buffer entry point staging
@@ -114,7 +116,7 @@ void free_all(gfm_ctx *h)
                     h->err, h->partials, h->dinfo, h->cc_parent, h->cc_size, h->cc_cand, h->cc_counters,
                     h->cc_bcount, h->cc_boff, h->cc_epart,
                     h->comp, h->cross, h->coarse, h->ftank, h->stank, h->tncell, h->tphys, h->tprm, h->cta,
-                    h->tank_cta, h->binfos};
+                    h->tank_cta, h->binfos, h->tcoff, h->tioff, h->tco};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *hptrs[] = {h->hinfo, h->tphys_h, h->tprm_h, h->binfos_h};
@@ -322,6 +324,7 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
         ba.tank_cta = h->tank_cta;
         ba.tprm = h->tprm;
         ba.infos = info_dev;
+        ba.tco = h->tco;
         kernel = gfm::batched_kernel(h->ht.max_width);
         GFM_CUDA(h, cudaMemsetAsync(info_dev, 0, sizeof(gfm_solve_info) * h->T, s));
     }
@@ -464,6 +467,9 @@ gfm_status alloc_batch(gfm_ctx *h, cudaStream_t s)
     if (e == cudaSuccess) e = dalloc(&h->cta, (size_t)h->max_grid);
     if (e == cudaSuccess) e = dalloc(&h->tank_cta, (size_t)T);
     if (e == cudaSuccess) e = dalloc(&h->binfos, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&h->tcoff, (size_t)T + 1);
+    if (e == cudaSuccess) e = dalloc(&h->tioff, (size_t)T + 1);
+    if (e == cudaSuccess) e = dalloc(&h->tco, (size_t)T);
     if (e != cudaSuccess) return fail(h, GFM_ERR_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
     if (cudaMallocHost((void **)&h->tphys_h, sizeof(gfm::TankPhys) * T) != cudaSuccess ||
         cudaMallocHost((void **)&h->tprm_h, sizeof(gfm::DevParams) * T) != cudaSuccess ||
@@ -472,6 +478,8 @@ gfm_status alloc_batch(gfm_ctx *h, cudaStream_t s)
     e = cudaMemcpyAsync(h->ftank, h->bt.face_tank.data(), sizeof(int32_t) * h->F, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->stank, h->bt.slice_tank.data(), sizeof(int32_t) * h->ht.n_slices, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tncell, h->bt.ncell.data(), sizeof(int32_t) * T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tcoff, h->bt.coff.data(), sizeof(int32_t) * (T + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tioff, h->bt.ioff.data(), sizeof(int32_t) * (T + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "uploading batch tables");
     return GFM_OK;
@@ -654,7 +662,7 @@ gfm_status gfm_create_batched(const gfm_mesh *meshes, int32_t n_tanks, int32_t r
         h->F = (int)nface;
         h->batched = true;
         h->T = n_tanks;
-        h->coarse_max = 0;  // the coarse space is per mesh; batched tanks run Jacobi
+        h->coarse_max = gfm::kTankCoarse;  // per tank: the water body and the air above it
         st = alloc_upload(h, s);
         if (st != GFM_OK) break;
         st = alloc_batch(h, s);
@@ -784,8 +792,8 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     ca.tprm = h->batched ? h->tprm : nullptr;
     GFM_CUDA(h, gfm::launch_cells(ca, s));
     int launched = 2;
-    if (!h->batched) {
-        gfm::CoarseArgs co;
+    {
+        gfm::CoarseArgs co{};
         co.n = h->n;
         co.F = h->F;
         co.n_pad = h->ht.n_pad;
@@ -809,6 +817,14 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
         co.comp = h->comp;
         co.cross = h->cross;
         co.coarse = h->coarse;
+        if (h->batched) {  // one coarse space per tank
+            co.T = h->T;
+            co.coff = h->tcoff;
+            co.ioff = h->tioff;
+            co.tprm = h->tprm;
+            co.tco = h->tco;
+            co.max_k = std::min(h->coarse_max, gfm::kTankCoarse);
+        }
         GFM_CUDA(h, gfm::launch_coarse(co, s, &launched));
     }
     if (h->ref_internal < 0) {  // only an unpinned system needs sum(b) for its compatibility test
@@ -1095,6 +1111,22 @@ gfm_status gfm_get_coarse(gfm_handle h, int32_t *n_vectors, int32_t *n_regions, 
     gfm::Coarse co;
     cudaStream_t s = (cudaStream_t)stream;
     GFM_CUDA(h, cudaMemcpyAsync(&co, h->coarse, sizeof co, cudaMemcpyDeviceToHost, s));
+    if (h->batched) {  // vectors summed over the tanks; sizes of the first tanks' vectors
+        std::vector<gfm::TankCoarse> tc((size_t)h->T);
+        GFM_CUDA(h, cudaMemcpyAsync(tc.data(), h->tco, sizeof(gfm::TankCoarse) * h->T, cudaMemcpyDeviceToHost, s));
+        GFM_CUDA(h, cudaStreamSynchronize(s));
+        int nv = 0;
+        for (const auto &t : tc)
+            for (int k = 0; k < t.K; ++k) {
+                if (sizes && nv < gfm::kMaxCoarse) sizes[nv] = t.sizes[k];
+                ++nv;
+            }
+        if (sizes)
+            for (int k = nv; k < gfm::kMaxCoarse; ++k) sizes[k] = 0;
+        if (n_vectors) *n_vectors = nv;
+        if (n_regions) *n_regions = co.n_cand;
+        return GFM_OK;
+    }
     GFM_CUDA(h, cudaStreamSynchronize(s));
     if (n_vectors) *n_vectors = co.K;
     if (n_regions) *n_regions = co.n_cand;

@@ -324,6 +324,142 @@ __global__ void k_coarse_finish(const int8_t *__restrict__ comp, int ref, const 
     co->K = K;
 }
 
+// ---- batched handles: one coarse space per tank --------------------------
+
+// One warp per tank: its up-to-max_k (<= kTankCoarse) largest regions among
+// the candidates whose root lies in the tank (ties: smaller root first).
+__global__ void k_cc_select_tanks(const int *__restrict__ csize, const int *__restrict__ cand, int *counters,
+                                  int max_k, const int32_t *__restrict__ coff, const DevParams *__restrict__ tprm,
+                                  Coarse *co, TankCoarse *tco)
+{
+    const int t = blockIdx.x, lane = threadIdx.x;
+    const int nc = min(counters[0], kMaxCandidates);
+    const int lo = coff[t], hi = coff[t + 1];
+    int K = 0;
+    int chosen[kTankCoarse];
+    if (tprm[t].ref >= 0) {
+        for (int k = 0; k < max_k && k < kTankCoarse; ++k) {
+            long long best = -1;  // key = size * 2^32 + (2^31 - 1 - root)
+            for (int q = lane; q < nc; q += 32) {
+                const int c = cand[q];
+                if (c < lo || c >= hi) continue;
+                bool taken = false;
+                for (int j = 0; j < K; ++j) taken |= (chosen[j] == c);
+                if (taken) continue;
+                const long long key = ((long long)csize[c] << 32) | (long long)(0x7fffffff - c);
+                if (key > best) best = key;
+            }
+            for (int off = 16; off; off >>= 1) {
+                const long long o = __shfl_xor_sync(0xffffffffu, best, off);
+                if (o > best) best = o;
+            }
+            if (best < 0) break;
+            chosen[K++] = 0x7fffffff - (int)(best & 0xffffffffLL);
+        }
+    }
+    if (lane == 0) {
+        TankCoarse &c = tco[t];
+        c.K = K;
+        c.ref_comp = -1;
+        c.x0 = c.x1 = 0;
+        for (int k = 0; k < kTankCoarse; ++k) {
+            c.roots[k] = k < K ? chosen[k] : -1;
+            c.sizes[k] = k < K ? csize[chosen[k]] : 0;
+        }
+        for (int q = 0; q < kTankCoarse * kTankCoarse; ++q) c.E[q] = c.Einv[q] = 0.0;
+        if (t == 0) {  // the cross-face kernels run when any tank may have regions
+            co->K = 1;
+            co->n_cand = counters[0];
+            co->n_cross = 0;
+            co->ref_comp = -1;
+            counters[1] = 0;
+        }
+    }
+}
+
+__global__ void k_cc_label_tanks(int n, int T, int *parent, const int32_t *__restrict__ perm,
+                                 const int32_t *__restrict__ coff, const TankCoarse *__restrict__ tco, int8_t *comp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = T;  // the tank t with coff[t] <= i < coff[t+1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (coff[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    const int r = cc_find(parent, i);
+    int id = -1;
+    for (int k = 0; k < tco[lo].K; ++k)
+        if (tco[lo].roots[k] == r) id = k;
+    comp[perm[i]] = (int8_t)id;
+}
+
+// One warp per tank: its stretch of the cross-face list (face order puts the
+// tanks one after another), E = Z^T A Z summed in a fixed order, the pin,
+// and the inverse (K <= 2: closed form, K = 0 if not positive definite).
+__global__ void k_coarse_tanks(const CrossFace *__restrict__ cross, const int *__restrict__ counters, int max_cross,
+                               const int32_t *__restrict__ ioff, int T, const int8_t *__restrict__ comp,
+                               const DevParams *__restrict__ tprm, TankCoarse *tco)
+{
+    const int t = blockIdx.x, lane = threadIdx.x;
+    const int nx = min(counters[1], max_cross);
+    auto first_of = [&](int tank) {
+        if (tank >= T) return nx;
+        int lo = 0, hi = nx;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cross[mid].o < ioff[tank]) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int x0 = first_of(t), x1 = first_of(t + 1);
+    double e00 = 0.0, e01 = 0.0, e11 = 0.0;
+    for (int q = x0 + lane; q < x1; q += 32) {
+        const CrossFace cf = cross[q];
+        const double g = cf.g64;
+        if (cf.a == 0 || cf.b == 0) e00 += g;
+        if (cf.a == 1 || cf.b == 1) e11 += g;
+        if ((cf.a == 0 && cf.b == 1) || (cf.a == 1 && cf.b == 0)) e01 -= g;
+    }
+    for (int off = 16; off; off >>= 1) {
+        e00 += __shfl_xor_sync(0xffffffffu, e00, off);
+        e01 += __shfl_xor_sync(0xffffffffu, e01, off);
+        e11 += __shfl_xor_sync(0xffffffffu, e11, off);
+    }
+    if (lane != 0) return;
+    TankCoarse &c = tco[t];
+    int K = c.K;
+    const int ref = tprm[t].ref;
+    const int rc = (K > 0 && ref >= 0) ? comp[ref] : -1;
+    double E[4] = {e00, e01, e01, e11};
+    if (rc >= 0) E[rc * 3] += tprm[t].pin64;  // E[0] or E[3]
+    double inv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (K == 1) {
+        if (E[0] > 0.0) inv[0] = 1.0 / E[0];
+        else K = 0;
+    } else if (K == 2) {
+        const double det = E[0] * E[3] - E[1] * E[2];
+        if (E[0] > 0.0 && det > 0.0) {
+            inv[0] = E[3] / det;
+            inv[1] = -E[1] / det;
+            inv[2] = -E[2] / det;
+            inv[3] = E[0] / det;
+        } else {
+            K = 0;
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        c.E[q] = E[q];
+        c.Einv[q] = inv[q];
+    }
+    c.K = K;
+    c.ref_comp = K > 0 ? rc : -1;
+    c.x0 = x0;
+    c.x1 = x1;
+}
+
 inline int blocks_for(long long work, int threads) { return (int)((work + threads - 1) / threads); }
 
 }  // namespace
@@ -337,17 +473,27 @@ cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches)
     k_cc_hook<<<blocks_for(a.F, T), T, 0, s>>>(a.F, a.owner, a.neighbour, a.kind, a.parent);
     k_cc_count<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.csize);
     k_cc_candidates<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.csize, a.min_size, a.cand, a.counters);
-    k_cc_select<<<1, 32, 0, s>>>(a.csize, a.cand, a.counters, a.max_k, a.ref, a.coarse);
-    k_cc_label<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.perm, a.coarse, a.comp);
+    if (a.T > 0) {
+        k_cc_select_tanks<<<a.T, 32, 0, s>>>(a.csize, a.cand, a.counters, a.max_k, a.coff, a.tprm, a.coarse, a.tco);
+        k_cc_label_tanks<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.T, a.parent, a.perm, a.coff, a.tco, a.comp);
+    } else {
+        k_cc_select<<<1, 32, 0, s>>>(a.csize, a.cand, a.counters, a.max_k, a.ref, a.coarse);
+        k_cc_label<<<blocks_for(a.n, T), T, 0, s>>>(a.n, a.parent, a.perm, a.coarse, a.comp);
+    }
     const int nblk = blocks_for(a.F, T);
     k_cross_count<<<nblk, T, 0, s>>>(a.F, a.owner, a.neighbour, a.perm, a.comp, a.coarse, a.bcount);
     k_cross_scan<<<1, 1024, 0, s>>>(nblk, a.bcount, a.boff, a.counters);
     k_cross_write<<<nblk, T, 0, s>>>(a.F, a.owner, a.neighbour, a.perm, a.comp, a.gamma, a.coarse, a.boff, a.cross,
                                      a.max_cross);
-    k_coarse_E<<<kEBlocks, kEThreads, 0, s>>>(a.cross, a.counters, a.max_cross, a.coarse, a.epart);
-    k_coarse_finish<<<1, kMaxCoarse * kMaxCoarse, 0, s>>>(a.comp, a.ref, a.prm, a.coarse, a.counters, a.max_cross,
-                                                         a.epart);
-    if (launches) *launches += 11;
+    if (a.T > 0) {
+        k_coarse_tanks<<<a.T, 32, 0, s>>>(a.cross, a.counters, a.max_cross, a.ioff, a.T, a.comp, a.tprm, a.tco);
+        if (launches) *launches += 10;
+    } else {
+        k_coarse_E<<<kEBlocks, kEThreads, 0, s>>>(a.cross, a.counters, a.max_cross, a.coarse, a.epart);
+        k_coarse_finish<<<1, kMaxCoarse * kMaxCoarse, 0, s>>>(a.comp, a.ref, a.prm, a.coarse, a.counters,
+                                                             a.max_cross, a.epart);
+        if (launches) *launches += 11;
+    }
     return cudaGetLastError();
 }
 

@@ -39,6 +39,18 @@ struct Coarse {
     double Einv[kMaxCoarse * kMaxCoarse];
 };
 
+// Coarse space of one tank of a batch: its up-to-kTankCoarse largest
+// one-phase regions (typically the water body and the air above it), E =
+// Z^T A Z of those regions and its inverse, and the tank's stretch
+// [x0, x1) of the face-ordered cross-face list.
+constexpr int kTankCoarse = 2;
+struct TankCoarse {
+    int32_t K, ref_comp, x0, x1;
+    int32_t roots[kTankCoarse], sizes[kTankCoarse];
+    double E[kTankCoarse * kTankCoarse];
+    double Einv[kTankCoarse * kTankCoarse];
+};
+
 // One face between two coarse regions: internal cell indices, coefficient,
 // and the regions (a of cell o, b of cell v; -1 = not in a coarse region).
 struct CrossFace {
@@ -154,6 +166,12 @@ struct CoarseArgs {
     int8_t *comp;  // internal order
     CrossFace *cross;
     Coarse *coarse;
+    // batched handles (T > 0): coarse regions are chosen per tank (region ids
+    // in comp are tank-local)
+    int32_t T;
+    const int32_t *coff, *ioff;  // [T+1] caller / internal cell offsets of the tanks
+    const DevParams *tprm;       // [T] pinned cell and pin of each tank
+    TankCoarse *tco;             // [T]
 };
 cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches);
 
@@ -190,6 +208,7 @@ struct BatchArgs {
     const int2 *tank_cta;
     const DevParams *tprm;
     gfm_solve_info *infos;  // [T]
+    const TankCoarse *tco;  // [T] coarse space of each tank
 };
 const void *batched_kernel(int max_width);
 

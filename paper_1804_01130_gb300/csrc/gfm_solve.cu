@@ -665,11 +665,9 @@ __device__ __forceinline__ void zero_bins(Shared &sh)
 // warp order: the same result at every run, and no shared-memory atomics
 // serialised on the two words of the water/air region pair.
 template <typename T, typename ValFn>
-__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, int K, T (*wbins)[kMaxCoarse],
-                                           ValFn val)
+__device__ __forceinline__ void cross_sums_range(const CrossFace *cross, int f0, int f1, int K,
+                                                 T (*wbins)[kMaxCoarse], ValFn val)
 {
-    const int f0 = (int)(((long long)n_cross * blockIdx.x) / gridDim.x);
-    const int f1 = (int)(((long long)n_cross * (blockIdx.x + 1)) / gridDim.x);
     T acc[kMaxCoarse];
 #pragma unroll
     for (int k = 0; k < kMaxCoarse; ++k) acc[k] = T(0);
@@ -700,6 +698,16 @@ __device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, 
         }
         if (lane == 0) wbins[warp][k] = any ? x : T(0);
     }
+}
+
+// The CTA's even share of all n_cross cross faces.
+template <typename T, typename ValFn>
+__device__ __forceinline__ void cross_sums(const CrossFace *cross, int n_cross, int K, T (*wbins)[kMaxCoarse],
+                                           ValFn val)
+{
+    const int f0 = (int)(((long long)n_cross * blockIdx.x) / gridDim.x);
+    const int f1 = (int)(((long long)n_cross * (blockIdx.x + 1)) / gridDim.x);
+    cross_sums_range<T>(cross, f0, f1, K, wbins, val);
 }
 
 // Warp 0, after a CTA barrier that follows cross_sums: bins[k] = the warps'
@@ -1207,6 +1215,70 @@ __device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_en
     }
 }
 
+
+// The same group for tables read from global memory (a CTA whose slots do not
+// fit in shared memory and are not streamed): every index and coefficient of
+// a chunk is loaded first, then every gather, so a chunk costs two dependent
+// memory round trips.
+template <int CH, int U, typename TabT>
+__device__ __forceinline__ void mixed_op_group_hoisted(const TabT &tab, int sb, int s_end, const Range &R, int n,
+                                                       const float2 *cur, float *P32, float *S32, float be, int ref,
+                                                       float pin32, int rc, int K, Shared &sh, FF &acc)
+{
+    int ii[U], base[U], w[U];
+    float2 v[U];
+    float pn[U], si[U];
+    int wmax = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int s = sb + u * R.nw;
+        ii[u] = s * kSlice + R.lane;
+        base[u] = 0;
+        w[u] = 0;
+        const bool act = s < s_end && ii[u] < n;
+        if (act) {
+            const Row rw = tab.row(s);
+            base[u] = rw.base;
+            w[u] = rw.w;
+        }
+        v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
+        pn[u] = fmaf(be, v[u].y, v[u].x);
+        si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+        wmax = max(wmax, w[u]);
+    }
+    for (int k0 = 0; k0 < wmax; k0 += CH) {
+        int j[U][CH];
+        float gm[U][CH];
+        float2 vj[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const bool ok = k0 + c < w[u];
+                const int slot = base[u] + (k0 + c) * kSlice + R.lane;
+                j[u][c] = ok ? tab.c(slot) : 0;
+                gm[u][c] = ok ? tab.v(slot) : 0.0f;
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (sb + u * R.nw < s_end && ii[u] < n) {
+            P32[ii[u]] = pn[u];
+            S32[ii[u]] = si[u];
+            ff_add(acc, pn[u] * si[u]);
+            if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p
+        }
+    }
+}
+
 }  // namespace
 
 template <int CH, bool STREAM>
@@ -1479,8 +1551,15 @@ namespace {
 struct TankState {
     double bnorm[kMaxTanks], sc[kMaxTanks], isc[kMaxTanks], gam[kMaxTanks], gam_prev[kMaxTanks];
     double rho_max[kMaxTanks], best[kMaxTanks], rho_stop[kMaxTanks], xavg[kMaxTanks];
-    double tot[4][kMaxTanks];
+    double tot[6][kMaxTanks];
     float al[kMaxTanks], be[kMaxTanks];
+    // each tank's coarse space: K vectors, region of the pinned cell, stretch
+    // [x0, x1) of the cross-face list, E^{-1}; y = Z^T r (FP64 recurrence)
+    // and the correction c = E^{-1} y (FP32, added to u)
+    int K[kMaxTanks], rc[kMaxTanks], x0[kMaxTanks], x1[kMaxTanks];
+    double Einv[kTankCoarse * kTankCoarse][kMaxTanks];
+    double y[kTankCoarse][kMaxTanks];
+    float c32[kTankCoarse][kMaxTanks];
     int act[kMaxTanks];   // kGo while iterating, else kConverged / kNotConverged / kBreakdown
     int flag[kMaxTanks];  // pending replacement: 0, kUpdate, kRestart, kNotConverged
     int iters[kMaxTanks], updates[kMaxTanks], stall[kMaxTanks], last_upd[kMaxTanks], restarts[kMaxTanks];
@@ -1513,6 +1592,20 @@ __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &
     return true;
 }
 
+// One lane, one tank: c = E^{-1} y into ts.c32 (K <= 2); returns y.c.
+__device__ __forceinline__ double tank_coarse_solve(TankState &ts, int t)
+{
+    const int K = ts.K[t];
+    double yc = 0.0;
+    for (int i = 0; i < K; ++i) {
+        double c = 0.0;
+        for (int j = 0; j < K; ++j) c = fma(ts.Einv[i * kTankCoarse + j][t], ts.y[j][t], c);
+        ts.c32[i][t] = (float)c;
+        yc = fma(c, ts.y[i][t], yc);
+    }
+    return yc;
+}
+
 // Residual replacement for the tanks with a pending flag (or all, `all`):
 // x += e / sc (FP64, when `fold`), r = b - A x (FP64, difference form),
 // r32 = (float)(r sc), u = r32 / D into up (direction cleared on restart).
@@ -1539,7 +1632,7 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
         if (!grid_sync(g, sh)) return false;  // x complete
     }
     double vr[1] = {0.0};
-    FF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    FF acc[2 + kTankCoarse] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (work) {
         for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
             const int i = s * kSlice + R.lane;
@@ -1554,14 +1647,40 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
                 else up[i].x = u;
                 ff_add(acc[0], r32 * u);
                 ff_add(acc[1], r32 * r32);
+                const int cm = a.comp[i];
+#pragma unroll
+                for (int k = 0; k < kTankCoarse; ++k) ff_add(acc[2 + k], (cm == k) ? r32 : 0.0f);
             }
         }
     }
     block_sum_f64<1>(sh, vr);
-    double ffo[2];
-    block_sum_ff<2>(sh, acc, ffo);
-    const double blk[3] = {vr[0], ffo[0], ffo[1]};
-    return batch_allreduce<3>(g, sh, ts, bt, blk);
+    double ffo[2 + kTankCoarse];
+    block_sum_ff<2 + kTankCoarse>(sh, acc, ffo);
+    const double blk[3 + kTankCoarse] = {vr[0], ffo[0], ffo[1], ffo[2], ffo[3]};
+    if (!batch_allreduce<3 + kTankCoarse>(g, sh, ts, bt, blk)) return false;
+    // replaced tanks: y = Z^T r exactly, c = E^{-1} y, r.z gains y.c, and the
+    // coarse correction joins u
+    int any_coarse = 0;
+    if (threadIdx.x < 32) {
+        for (int t = threadIdx.x; t < bt.T; t += 32) {
+            if (!(all || ts.flag[t] != 0) || ts.K[t] == 0) continue;
+            for (int k = 0; k < ts.K[t]; ++k) ts.y[k][t] = ts.tot[3 + k][t];
+            ts.tot[1][t] += tank_coarse_solve(ts, t);
+            any_coarse = 1;
+        }
+        any_coarse = __any_sync(0xffffffffu, any_coarse);
+        if (threadIdx.x == 0) sh.flag = any_coarse;
+    }
+    __syncthreads();
+    if (sh.flag == 0) return true;  // the same in every CTA
+    __syncthreads();
+    if (work && ts.K[tank] > 0) {
+        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+            const int i = s * kSlice + R.lane;
+            if (i < cend && a.comp[i] >= 0) up[i].x += ts.c32[a.comp[i]][tank];
+        }
+    }
+    return grid_sync(g, sh);  // u complete before it is gathered
 }
 
 __device__ void batch_abort(const SolveArgs &a, const BatchArgs &bt)
@@ -1637,6 +1756,16 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             ts.iters[t] = ts.updates[t] = ts.stall[t] = ts.last_upd[t] = ts.restarts[t] = 0;
             ts.be[t] = 0.0f;
             ts.gam_prev[t] = 1.0;
+            const TankCoarse &tc = bt.tco[t];
+            ts.K[t] = tc.K;
+            ts.rc[t] = tc.ref_comp;
+            ts.x0[t] = tc.x0;
+            ts.x1[t] = tc.x1;
+            for (int q = 0; q < kTankCoarse * kTankCoarse; ++q) ts.Einv[q][t] = tc.Einv[q];
+            for (int k = 0; k < kTankCoarse; ++k) {
+                ts.y[k][t] = 0.0;
+                ts.c32[k][t] = 0.0f;
+            }
         }
     }
     __syncthreads();
@@ -1663,67 +1792,37 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     while (ts.any_active) {
         const bool work = ts.act[tank] == kGo;
         const float be = ts.be[tank];
-        // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s
+        // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s,
+        // and the tank's Z^T (A p) from its faces between coarse regions
+        const int Kt = ts.K[tank];
+        zero_bins(sh);
+        __syncthreads();
         FF accA[1] = {{0.f, 0.f}};
         if (work) {
-            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw) {
-                int ii[U], base[U], w[U];
-                float2 v[U];
-                float pn[U], si[U];
-                int wmax = 0;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int s = sb + u * R.nw;
-                    ii[u] = s * kSlice + R.lane;
-                    base[u] = 0;
-                    w[u] = 0;
-                    const bool act = s < R.s1 && ii[u] < cend;
-                    if (act) {
-                        const Row rw = tab.row(s);
-                        base[u] = rw.base;
-                        w[u] = rw.w;
-                    }
-                    v[u] = act ? cur[ii[u]] : make_float2(0.f, 0.f);
-                    pn[u] = fmaf(be, v[u].y, v[u].x);
-                    si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
-                    wmax = max(wmax, w[u]);
-                }
-                for (int k0 = 0; k0 < wmax; k0 += CH) {
-                    int j[U][CH];
-                    float gm[U][CH];
-                    float2 vj[U][CH];
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            const bool ok = k0 + c < w[u];
-                            const int slot = base[u] + (k0 + c) * kSlice + R.lane;
-                            j[u][c] = ok ? tab.c(slot) : 0;
-                            gm[u][c] = ok ? tab.v(slot) : 0.0f;
-                        }
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) vj[u][c] = (k0 + c < w[u]) ? cur[j[u][c]] : v[u];
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-#pragma unroll
-                        for (int c = 0; c < CH; ++c)
-                            si[u] = fmaf(gm[u][c], pn[u] - fmaf(be, vj[u][c].y, vj[u][c].x), si[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (sb + u * R.nw < R.s1 && ii[u] < cend) {
-                        P32[ii[u]] = pn[u];
-                        S32[ii[u]] = si[u];
-                        ff_add(accA[0], pn[u] * si[u]);
-                    }
-                }
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
+                mixed_op_group_hoisted<CH, U>(tab, sb, R.s1, R, cend, cur, P32, S32, be, ref, pin32, ts.rc[tank], Kt,
+                                              sh, accA[0]);
+            if (Kt > 0) {
+                // this CTA's share of the tank's cross faces
+                const int2 tr = bt.tank_cta[tank];
+                const long long q = blockIdx.x - tr.x, nq = tr.y - tr.x, span = ts.x1[tank] - ts.x0[tank];
+                cross_sums_range<float>(a.cross, ts.x0[tank] + (int)(span * q / nq),
+                                        ts.x0[tank] + (int)(span * (q + 1) / nq), Kt, sh.zbw32,
+                                        [&](const CrossFace &cf) {
+                                            const float2 vo = cur[cf.o], vv = cur[cf.v];
+                                            return cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
+                                        });
             }
         }
-        double blkA[1];
-        block_sum_ff<1>(sh, accA, blkA);
-        if (!batch_allreduce<1>(g, sh, ts, bt, blkA)) { batch_abort(a, bt); return; }
+        double blkA[1 + kTankCoarse];
+        {
+            double b1[1];
+            block_sum_ff<1>(sh, accA, b1);
+            blkA[0] = b1[0];
+        }
+        if (work && Kt > 0 && threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, ts.rc[tank], Kt, R.nw, sh.zb32);
+        for (int k = 0; k < kTankCoarse; ++k) blkA[1 + k] = (work && k < Kt) ? (double)sh.zb32[k] : 0.0;
+        if (!batch_allreduce<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { batch_abort(a, bt); return; }
         if (threadIdx.x < 32) {
             for (int t = threadIdx.x; t < T; t += 32) {
                 if (ts.act[t] != kGo) continue;
@@ -1731,6 +1830,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                 const bool ok = ps > 0.0 && isfinite(ps) && ts.gam[t] > 0.0;
                 ts.al[t] = ok ? (float)(ts.gam[t] / ps) : 0.0f;
                 ts.flag[t] = ok ? 0 : kRestart;
+                if (ok && ts.K[t] > 0) {  // y -= alpha Z^T A p, c = E^{-1} y
+                    for (int k = 0; k < ts.K[t]; ++k) ts.y[k][t] = fma(-(double)ts.al[t], ts.tot[1 + k][t], ts.y[k][t]);
+                    tank_coarse_solve(ts, t);
+                }
             }
         }
         __syncthreads();
@@ -1758,7 +1861,11 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                         E[ii[u]] = fmaf(al, pi[u], ei[u]);
                         const float rn = fmaf(-al, si[u], ri[u]);
                         R32[ii[u]] = rn;
-                        const float un = rn * di[u];
+                        float un = rn * di[u];
+                        if (Kt > 0) {
+                            const int cm = a.comp[ii[u]];
+                            if (cm >= 0) un += ts.c32[cm][tank];
+                        }
                         nxt[ii[u]] = make_float2(un, pi[u]);
                         ff_add(accB[0], rn * un);
                         ff_add(accB[1], rn * rn);
