@@ -198,6 +198,9 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
             max_slots = std::max(max_slots, h->ht.slice_ptr[(size_t)s1] - h->ht.slice_ptr[(size_t)s0]);
         }
     }
+    // the batched solve keeps one all-reduce's CTA partials ahead of its tables
+    const long long red_bytes = h->batched ? gfm::batch_red_bytes(grid) : 0;
+    budget -= red_bytes;
     const int meta_slots = (max_nsl + 1) & ~1;
     const long long meta_bytes = (long long)meta_slots * 8;
     const long long slot_bytes = 4 + (mode == gfm::Mode::FP64 ? 8 : 4);
@@ -225,7 +228,8 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
         }
         if (n_stages) cap = 0;
     }
-    const size_t dyn = (size_t)(meta_bytes + (n_stages ? (long long)n_stages * stage_cap * 8 : cap * slot_bytes));
+    const size_t dyn =
+        (size_t)(red_bytes + meta_bytes + (n_stages ? (long long)n_stages * stage_cap * 8 : cap * slot_bytes));
     if (n_stages) k = gfm::solver_kernel(mode, h->ht.max_width, t, true);
     GFM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int occ = 0;

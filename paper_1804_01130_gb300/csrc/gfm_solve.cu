@@ -1557,6 +1557,15 @@ struct TankState {
     // [x0, x1) of the cross-face list, E^{-1}; y = Z^T r (FP64 recurrence)
     // and the correction c = E^{-1} y (FP32, added to u)
     int K[kMaxTanks], rc[kMaxTanks], x0[kMaxTanks], x1[kMaxTanks];
+    // CTAs of each tank [first, last + 1), re-planned when tanks finish, and
+    // each tank's slices [sfirst, sfirst + nslc) and end of its real cells
+    int2 tcta[kMaxTanks];
+    int sfirst[kMaxTanks], nslc[kMaxTanks], tend[kMaxTanks];
+    int n_active;
+    // tanks with more than kLaneSum CTAs, whose partials a whole warp sums
+    int wide[kMaxTanks];
+    int n_wide;
+    double *red;  // dynamic shared memory: [kBatchNR][G] CTA partials
     double Einv[kTankCoarse * kTankCoarse][kMaxTanks];
     double y[kTankCoarse][kMaxTanks];
     float c32[kTankCoarse][kMaxTanks];
@@ -1566,30 +1575,58 @@ struct TankState {
     int any_flag, any_active;
 };
 
-// Per-tank all-reduce: CTA partials as in grid_allreduce, then warp k sums
-// value k for every tank over that tank's CTAs (fixed order) into ts.tot[k].
+// Per-tank all-reduce.  Every CTA writes its partials, and after the grid
+// barrier copies all of them (one coalesced read) into shared memory; then
+// value k of tank t is the sum over the tank's CTAs in CTA order, by one
+// thread when the tank has at most kLaneSum CTAs, else by one warp (lane l
+// takes CTAs l, l + 32, ..., then a fixed butterfly).  Which rule a tank gets
+// depends only on the CTA table, which every CTA holds, so every CTA gets the
+// same bits.
 template <int NR>
 __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &ts, const BatchArgs &bt,
                                                 const double (&blk)[NR])
 {
+    static_assert(NR <= kBatchNR, "batched reduction buffer too small");
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NR; ++k) g.partials[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
     }
     if (!grid_sync(g, sh)) return false;
+    const int G = g.G, T = bt.T;
+    double *red = ts.red;
+    const double *src = g.partials + (size_t)g.parity * kMaxNR * G;
+    for (int i = threadIdx.x; i < NR * G; i += blockDim.x) red[i] = __ldcg(src + i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < NR * T; i += blockDim.x) {
+        const int k = i / T, t = i - k * T;
+        const int2 r = ts.tcta[t];
+        if (r.y - r.x > kLaneSum) continue;
+        double acc = 0.0;
+        for (int c = r.x; c < r.y; ++c) acc += red[k * G + c];
+        ts.tot[k][t] = acc;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int k = warp; k < NR; k += nw) {
-        const double *src = g.partials + ((size_t)g.parity * kMaxNR + k) * g.G;
-        for (int t = lane; t < bt.T; t += 32) {
-            const int2 r = bt.tank_cta[t];
-            double acc = 0.0;
-            for (int c = r.x; c < r.y; ++c) acc += __ldcg(src + c);
-            ts.tot[k][t] = acc;
-        }
+    for (int i = warp; i < NR * ts.n_wide; i += nw) {
+        const int k = i / ts.n_wide, t = ts.wide[i - k * ts.n_wide];
+        const int2 r = ts.tcta[t];
+        double acc = 0.0;
+        for (int c = r.x + lane; c < r.y; c += 32) acc += red[k * G + c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) ts.tot[k][t] = acc;
     }
     g.parity ^= 1;
     __syncthreads();
     return true;
+}
+
+// Thread 0: list the tanks whose CTA count calls for a warp-wide sum.
+__device__ __forceinline__ void list_wide(TankState &ts, int T)
+{
+    int n = 0;
+    for (int t = 0; t < T; ++t)
+        if (ts.tcta[t].y - ts.tcta[t].x > kLaneSum) ts.wide[n++] = t;
+    ts.n_wide = n;
 }
 
 // One lane, one tank: c = E^{-1} y into ts.c32 (K <= 2); returns y.c.
@@ -1683,6 +1720,117 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
     return grid_sync(g, sh);  // u complete before it is gathered
 }
 
+// Thread 0 of every CTA: split the grid among the tanks that still iterate
+// (all tanks when `all`): each gets one CTA plus a share of the rest in
+// proportion to its slices (largest remainders first, ties to the lower
+// tank); tanks left out get no CTA.  A pure function of the active set,
+// which every CTA holds, so every CTA builds the same table.
+__device__ void batch_rebalance(TankState &ts, int T, int G, bool all)
+{
+    long long total = 0;
+    int nact = 0;
+    for (int t = 0; t < T; ++t)
+        if (all || ts.act[t] == kGo) {
+            total += ts.nslc[t];
+            ++nact;
+        }
+    if (nact == 0) return;
+    if (total <= 0) total = 1;
+    const long long extra = G - nact;
+    bool got[kMaxTanks];
+    int given = 0;
+    for (int t = 0; t < T; ++t) {
+        const bool on = all || ts.act[t] == kGo;
+        const int g = on ? 1 + (int)((extra * ts.nslc[t]) / total) : 0;
+        ts.tcta[t] = make_int2(0, g);  // .y holds the count for now
+        got[t] = !on;
+        given += g;
+    }
+    for (int left = G - given; left > 0; --left) {  // one more to the largest remainders
+        int best = -1;
+        long long bestr = -1;
+        for (int t = 0; t < T; ++t) {
+            if (got[t]) continue;
+            const long long r = (extra * ts.nslc[t]) % total;
+            if (r > bestr) {
+                bestr = r;
+                best = t;
+            }
+        }
+        if (best < 0) break;
+        got[best] = true;
+        ts.tcta[best].y += 1;
+    }
+    int c = 0;
+    for (int t = 0; t < T; ++t) {
+        const int g = ts.tcta[t].y;
+        ts.tcta[t] = make_int2(c, c + g);
+        c += g;
+    }
+    list_wide(ts, T);
+}
+
+// Slice tables of the batched solve, staged in shared memory like the
+// single-mesh ones (the slices' (base, width) and the first slots of the
+// range) and staged again whenever a re-plan hands the CTA other slices.  A
+// range longer than the metadata area reads the rest of its metadata from
+// global memory.
+struct BTab {
+    const int2 *meta;
+    const int32_t *col;
+    const float *val;
+    const int32_t *gptr, *gcol;
+    const float *gval;
+    int s0, nmeta, base0, end;
+    __device__ __forceinline__ Row row(int s) const
+    {
+        const int k = s - s0;
+        if (k < nmeta) {
+            const int2 m = meta[k];
+            return Row{m.x, m.y};
+        }
+        const int b = __ldg(gptr + s);
+        return Row{b, (__ldg(gptr + s + 1) - b) >> 5};
+    }
+    __device__ __forceinline__ int c(int slot) const { return slot < end ? col[slot - base0] : __ldg(gcol + slot); }
+    __device__ __forceinline__ float v(int slot) const { return slot < end ? val[slot - base0] : __ldg(gval + slot); }
+};
+
+// All threads: stage the range's tables (ends with a block barrier; the
+// caller makes sure nobody still reads the previous ones).
+__device__ BTab stage_btab(const Sell &m, const Range &R, int cache_cap, int meta_slots, unsigned char *dsm)
+{
+    BTab t;
+    int2 *meta = reinterpret_cast<int2 *>(dsm);
+    int32_t *col = reinterpret_cast<int32_t *>(dsm + (size_t)meta_slots * sizeof(int2));
+    float *val = reinterpret_cast<float *>(dsm + (size_t)meta_slots * sizeof(int2) + (size_t)cache_cap * sizeof(int32_t));
+    const int nsl = R.s1 - R.s0;
+    const int nmeta = min(nsl, meta_slots);
+    for (int k = threadIdx.x; k < nmeta; k += blockDim.x) {
+        const int b = __ldg(m.slice_ptr + R.s0 + k);
+        meta[k] = make_int2(b, (__ldg(m.slice_ptr + R.s0 + k + 1) - b) >> 5);
+    }
+    const int base0 = (nsl > 0) ? __ldg(m.slice_ptr + R.s0) : 0;
+    const int total = (nsl > 0) ? __ldg(m.slice_ptr + R.s1) - base0 : 0;
+    const int cap = min(total, cache_cap);
+    for (int k = threadIdx.x; k < cap; k += blockDim.x) {
+        col[k] = __ldg(m.col + base0 + k);
+        val[k] = __ldg(m.val32 + base0 + k);
+    }
+    __syncthreads();
+    t.meta = meta;
+    t.col = col;
+    t.val = val;
+    t.gptr = m.slice_ptr;
+    t.gcol = m.col;
+    t.gval = m.val32;
+    t.s0 = R.s0;
+    t.nmeta = nmeta;
+    t.base0 = base0;
+    t.end = base0 + cap;
+    return t;
+}
+
 __device__ void batch_abort(const SolveArgs &a, const BatchArgs &bt)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1706,20 +1854,53 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     __shared__ TankState ts;
     extern __shared__ __align__(16) unsigned char dsm[];
     Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
+    const int T = bt.T;
+    // dynamic shared memory: the reduction buffer, then the staged tables
+    unsigned char *tdsm = dsm + batch_red_bytes((int)gridDim.x);
+    // this CTA's tank and slices: from the planned table at first, from the
+    // re-planned one (ts.tcta) once tanks have finished
     const int4 me = bt.cta[blockIdx.x];
-    const int tank = me.x, cend = me.w;
+    int tank = me.x, cend = me.w;
     Range R;
     R.s0 = me.y;
     R.s1 = me.z;
     R.warp = threadIdx.x >> 5;
     R.lane = threadIdx.x & 31;
     R.nw = blockDim.x >> 5;
-    const Tab<float> tab = stage_tables<float>(a.m, a.m.val32, R, a.cache_cap, a.meta_slots, dsm);
-    const DevParams pm = bt.tprm[tank];
-    const int ref = pm.ref;
-    const float pin32 = pm.pin32;
-    const double pin64 = pm.pin64;
-    const int T = bt.T;
+    DevParams pm = bt.tprm[tank];
+    int ref = pm.ref;
+    float pin32 = pm.pin32;
+    double pin64 = pm.pin64;
+    if (threadIdx.x < 32) {
+        for (int t = threadIdx.x; t < T; t += 32) {
+            const int2 r = bt.tank_cta[t];
+            ts.tcta[t] = r;
+            ts.sfirst[t] = bt.cta[r.x].y;
+            ts.nslc[t] = bt.cta[r.y - 1].z - bt.cta[r.x].y;
+            ts.tend[t] = bt.cta[r.x].w;
+        }
+    }
+    if (threadIdx.x == 0) {
+        ts.red = reinterpret_cast<double *>(dsm);
+        list_wide(ts, T);
+    }
+    BTab tab = stage_btab(a.m, R, a.cache_cap, a.meta_slots, tdsm);  // ends with a block barrier
+    // after a re-plan: find this CTA's tank and its share of the tank's slices
+    auto take_assignment = [&]() {
+        int t = 0;
+        while (t < T - 1 && !(ts.tcta[t].x <= (int)blockIdx.x && (int)blockIdx.x < ts.tcta[t].y)) ++t;
+        const int2 r = ts.tcta[t];
+        const long long q = blockIdx.x - r.x, nq = r.y - r.x;
+        tank = t;
+        cend = ts.tend[t];
+        R.s0 = ts.sfirst[t] + (int)((ts.nslc[t] * q) / nq);
+        R.s1 = ts.sfirst[t] + (int)((ts.nslc[t] * (q + 1)) / nq);
+        pm = bt.tprm[t];
+        ref = pm.ref;
+        pin32 = pm.pin32;
+        pin64 = pm.pin64;
+        tab = stage_btab(a.m, R, a.cache_cap, a.meta_slots, tdsm);
+    };
     float *__restrict__ E = a.E;
     float *__restrict__ R32 = a.R32;
     float *__restrict__ S32 = a.S32;
@@ -1789,6 +1970,8 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         if (threadIdx.x == 0) ts.any_active = active;
     }
     __syncthreads();
+    if (threadIdx.x == 0) ts.n_active = T;  // re-plan as soon as any tank is done
+    __syncthreads();
     while (ts.any_active) {
         const bool work = ts.act[tank] == kGo;
         const float be = ts.be[tank];
@@ -1804,7 +1987,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                                               sh, accA[0]);
             if (Kt > 0) {
                 // this CTA's share of the tank's cross faces
-                const int2 tr = bt.tank_cta[tank];
+                const int2 tr = ts.tcta[tank];
                 const long long q = blockIdx.x - tr.x, nq = tr.y - tr.x, span = ts.x1[tank] - ts.x0[tank];
                 cross_sums_range<float>(a.cross, ts.x0[tank] + (int)(span * q / nq),
                                         ts.x0[tank] + (int)(span * (q + 1) / nq), Kt, sh.zbw32,
@@ -1933,14 +2116,24 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             }
             __syncthreads();
         }
-        if (threadIdx.x < 32) {
-            bool active = false;
-            for (int t = threadIdx.x; t < T; t += 32) active |= ts.act[t] == kGo;
-            active = __any_sync(0xffffffffu, active);
-            if (threadIdx.x == 0) ts.any_active = active;
+        if (threadIdx.x == 0) {
+            int nact = 0;
+            for (int t = 0; t < T; ++t) nact += ts.act[t] == kGo;
+            ts.any_active = nact > 0;
+            sh.flag = (nact > 0 && nact < ts.n_active);  // tanks finished: re-plan
+            if (sh.flag) {
+                ts.n_active = nact;
+                batch_rebalance(ts, T, (int)gridDim.x, false);
+            }
         }
         __syncthreads();
+        if (sh.flag) take_assignment();
+        __syncthreads();
     }
+    // every tank gets CTAs again for the final residuals
+    if (threadIdx.x == 0) batch_rebalance(ts, T, (int)gridDim.x, true);
+    __syncthreads();
+    take_assignment();
     // per-tank finish: true residual, solution in caller order, L1 residual
     if (!grid_sync(g, sh)) { batch_abort(a, bt); return; }
     double v[2] = {0.0, 0.0};
