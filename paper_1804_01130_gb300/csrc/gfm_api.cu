@@ -191,6 +191,9 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
             max_nsl = std::max(max_nsl, s1 - s0);
             max_slots = std::max(max_slots, h->ht.slice_ptr[(size_t)s1] - h->ht.slice_ptr[(size_t)s0]);
         }
+        // the device re-plans the table as tanks finish: room for the
+        // metadata of any range it can hand out
+        max_nsl = std::max(max_nsl, gfm::batch_replan_max_slices(h->bt, grid));
     } else {
         for (int b = 0; b < grid; ++b) {
             const int s0 = (int)(((long long)ns * b) / grid), s1 = (int)(((long long)ns * (b + 1)) / grid);
@@ -213,7 +216,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     // = the slices the CTA's warps take at once: 4 per warp for rows of <= 6
     // faces, else 2).
     int n_stages = 0, stage_slices = 0, stage_cap = 0;
-    if (mode == gfm::Mode::MIXED && !h->batched && cap < max_slots) {
+    if (mode == gfm::Mode::MIXED && cap < max_slots) {
         const int maxw = std::max(1, h->ht.max_width);
         const int unit = (maxw <= 6 ? 4 : 2) * (t / 32);
         const long long per_unit = (long long)unit * 32 * maxw * 8;
@@ -230,7 +233,8 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     }
     const size_t dyn =
         (size_t)(red_bytes + meta_bytes + (n_stages ? (long long)n_stages * stage_cap * 8 : cap * slot_bytes));
-    if (n_stages) k = gfm::solver_kernel(mode, h->ht.max_width, t, true);
+    if (n_stages)
+        k = h->batched ? gfm::batched_kernel(h->ht.max_width, true) : gfm::solver_kernel(mode, h->ht.max_width, t, true);
     GFM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int occ = 0;
     GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, t, dyn));
@@ -329,7 +333,7 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
         ba.tprm = h->tprm;
         ba.infos = info_dev;
         ba.tco = h->tco;
-        kernel = gfm::batched_kernel(h->ht.max_width);
+        kernel = gfm::batched_kernel(h->ht.max_width, lp.n_stages > 0);
         GFM_CUDA(h, cudaMemsetAsync(info_dev, 0, sizeof(gfm_solve_info) * h->T, s));
     }
     void *args[] = {&a, &ba};

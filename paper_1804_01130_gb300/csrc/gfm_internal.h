@@ -215,7 +215,7 @@ struct BatchArgs {
     gfm_solve_info *infos;  // [T]
     const TankCoarse *tco;  // [T] coarse space of each tank
 };
-const void *batched_kernel(int max_width);
+const void *batched_kernel(int max_width, bool streamed = false);
 
 enum class Mode { FP64 = 0, MIXED = 1 };
 const void *solver_kernel(Mode m, int max_width, int threads, bool streamed = false);

@@ -370,4 +370,20 @@ bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4
     return true;
 }
 
+int batch_replan_max_slices(const BatchTables &bt, int grid)
+{
+    const int T = bt.T;
+    long long total = 0;
+    for (int k = 0; k < T; ++k) total += (bt.ioff[(size_t)k + 1] - bt.ioff[(size_t)k]) / kSliceH;
+    if (total <= 0) total = 1;
+    const long long extra = std::max(grid - T, 0);
+    int worst = 0;
+    for (int k = 0; k < T; ++k) {
+        const long long sl = (bt.ioff[(size_t)k + 1] - bt.ioff[(size_t)k]) / kSliceH;
+        const long long g = 1 + (extra * sl) / total;
+        worst = std::max(worst, (int)((sl + g - 1) / g));
+    }
+    return worst;
+}
+
 }  // namespace gfm

@@ -54,4 +54,11 @@ bool build_batch_tables(const std::vector<TankMesh> &tanks, int renumber, HostTa
 bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4, std::vector<int32_t> &tank2,
                      std::string &err, const std::vector<double> &weight = {});
 
+// Most slices one CTA can hold after the batched solve re-plans its CTA
+// table on the device.  A re-plan over a set S of tanks gives tank t
+// 1 + floor((grid - |S|) sl_t / sl_S) CTAs or one more (sl: slices), and a
+// CTA ceil(sl_t / CTAs) slices; (grid - |S|) / sl_S only grows as S shrinks,
+// so the plan over all tanks bounds every re-plan.
+int batch_replan_max_slices(const BatchTables &bt, int grid);
+
 }  // namespace gfm

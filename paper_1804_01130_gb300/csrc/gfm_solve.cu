@@ -502,6 +502,17 @@ __device__ Ring make_ring(const SolveArgs &a, const Range &R, const int2 *meta, 
     return g;
 }
 
+// Point an idle ring (every stage issued has been consumed or drained) at
+// the `nsl` slices from s0, whose metadata is staged at `meta`.
+__device__ __forceinline__ void ring_retarget(Ring &g, int s0, int nsl, const int2 *meta)
+{
+    g.meta = meta;
+    g.s0 = s0;
+    g.nsl = nsl;
+    g.nr = (nsl + g.stage_slices - 1) / g.stage_slices;
+    g.tab_end = nsl > 0 ? meta[nsl - 1].x + kSlice * meta[nsl - 1].y : 0;
+}
+
 // (A x)_i in FP64, difference form: sum_f gamma_f (x_i - x_j) + pin x_i.
 template <int CH>
 __device__ __forceinline__ double apply64_diff(const Sell &m, Row rw, int lane, const double *x, double xi,
@@ -1566,6 +1577,7 @@ struct TankState {
     int wide[kMaxTanks];
     int n_wide;
     double *red;  // dynamic shared memory: [kBatchNR][G] CTA partials
+    unsigned ring_used;  // thread 0's count of consumed stages after a drain
     double Einv[kTankCoarse * kTankCoarse][kMaxTanks];
     double y[kTankCoarse][kMaxTanks];
     float c32[kTankCoarse][kMaxTanks];
@@ -1845,11 +1857,12 @@ __device__ void batch_abort(const SolveArgs &a, const BatchArgs &bt)
 
 }  // namespace
 
-template <int CH>
+template <int CH, bool STREAM>
 __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs bt)
 {
-    constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass
-    constexpr int UB = 4;       // slices in flight per warp in the update pass
+    constexpr int U = 16 / CH;           // slices in flight per warp in the operator pass
+    constexpr int US = CH <= 6 ? 4 : 2;  // the same with streamed tables
+    constexpr int UB = 4;                // slices in flight per warp in the update pass
     __shared__ Shared sh;
     __shared__ TankState ts;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -1884,9 +1897,34 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         ts.red = reinterpret_cast<double *>(dsm);
         list_wide(ts, T);
     }
-    BTab tab = stage_btab(a.m, R, a.cache_cap, a.meta_slots, tdsm);  // ends with a block barrier
-    // after a re-plan: find this CTA's tank and its share of the tank's slices
-    auto take_assignment = [&]() {
+    BTab tab = stage_btab(a.m, R, STREAM ? 0 : a.cache_cap, a.meta_slots, tdsm);  // ends with a block barrier
+    // streamed tables: the ring follows the CTA's range; a range longer than
+    // the metadata area (the host sizes it for every re-plan) is an error
+    Ring ring{};
+    if constexpr (STREAM) {
+        ring = make_ring(a, R, tab.meta, tdsm, sh);
+        ring_retarget(ring, R.s0, tab.nmeta, tab.meta);
+        if (threadIdx.x == 0 && tab.nmeta < R.s1 - R.s0) atomicCAS(a.err, 0, (int)GFM_ERR_STATE);
+    }
+    // every early return first lets the stages still in flight land
+    auto bail = [&]() {
+        if constexpr (STREAM)
+            if (threadIdx.x == 0) ring_drain(ring, a.budget_ns);
+        batch_abort(a, bt);
+    };
+    // after a re-plan: find this CTA's tank and its share of the tank's
+    // slices, and stage its tables (a streamed ring is drained first and,
+    // with `prefetch`, asked for the new range's first stages)
+    auto take_assignment = [&](bool prefetch) {
+        if constexpr (STREAM) {
+            if (threadIdx.x == 0) {
+                ring_drain(ring, a.budget_ns);
+                if (ring.used != ring.issued) atomicCAS(a.err, 0, (int)GFM_ERR_TIMEOUT);
+                ts.ring_used = ring.used;
+            }
+            __syncthreads();
+            ring.used = ts.ring_used;
+        }
         int t = 0;
         while (t < T - 1 && !(ts.tcta[t].x <= (int)blockIdx.x && (int)blockIdx.x < ts.tcta[t].y)) ++t;
         const int2 r = ts.tcta[t];
@@ -1899,7 +1937,14 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         ref = pm.ref;
         pin32 = pm.pin32;
         pin64 = pm.pin64;
-        tab = stage_btab(a.m, R, a.cache_cap, a.meta_slots, tdsm);
+        tab = stage_btab(a.m, R, STREAM ? 0 : a.cache_cap, a.meta_slots, tdsm);
+        if constexpr (STREAM) {
+            ring_retarget(ring, R.s0, tab.nmeta, tab.meta);
+            if (threadIdx.x == 0) {
+                if (tab.nmeta < R.s1 - R.s0) atomicCAS(a.err, 0, (int)GFM_ERR_STATE);
+                if (prefetch) ring_prefetch(ring);
+            }
+        }
     };
     float *__restrict__ E = a.E;
     float *__restrict__ R32 = a.R32;
@@ -1921,7 +1966,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         }
     }
     block_sum_f64<1>(sh, vb);
-    if (!batch_allreduce<1>(g, sh, ts, bt, vb)) { batch_abort(a, bt); return; }
+    if (!batch_allreduce<1>(g, sh, ts, bt, vb)) { bail(); return; }
     if (threadIdx.x < 32) {
         for (int t = threadIdx.x; t < T; t += 32) {
             const double bb = ts.tot[0][t];
@@ -1952,7 +1997,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     __syncthreads();
     float2 *cur = a.UP0, *nxt = a.UP1;
     if (!batch_replace<CH>(a, bt, g, sh, ts, R, tank, cend, ref, pin64, cur, false, true)) {
-        batch_abort(a, bt);
+        bail();
         return;
     }
     if (threadIdx.x < 32) {
@@ -1970,7 +2015,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         if (threadIdx.x == 0) ts.any_active = active;
     }
     __syncthreads();
-    if (threadIdx.x == 0) ts.n_active = T;  // re-plan as soon as any tank is done
+    if (threadIdx.x == 0) {
+        ts.n_active = T;  // re-plan as soon as any tank is done
+        if constexpr (STREAM) ring_prefetch(ring);
+    }
     __syncthreads();
     while (ts.any_active) {
         const bool work = ts.act[tank] == kGo;
@@ -1981,10 +2029,40 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         zero_bins(sh);
         __syncthreads();
         FF accA[1] = {{0.f, 0.f}};
+        if constexpr (STREAM) {
+            // every stage is waited for, so the ring stays in step even when
+            // this CTA's tank has stopped
+            for (int r = 0; r < ring.nr; ++r) {
+                if (ring_wait(ring, a.budget_ns)) {
+                    if (work) {
+                        const int sr0 = ring.s0 + r * ring.stage_slices;
+                        const int sr1 = min(ring.s0 + ring.nsl, sr0 + ring.stage_slices);
+                        const StageTab st = ring_stage(ring, r);
+                        for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                            mixed_op_group<CH, US>(st, sb, sr1, R, cend, cur, P32, S32, be, ref, pin32, ts.rc[tank],
+                                                   Kt, sh, accA[0]);
+                    }
+                } else {
+                    sh.ring_fail = 1;
+                }
+                ++ring.used;
+                __syncthreads();  // stage consumed: it may be refilled
+                if (sh.ring_fail) break;
+                if (threadIdx.x == 0 && r + ring.n_stages < ring.nr) ring_issue(ring, r + ring.n_stages);
+            }
+            if (sh.ring_fail) {
+                if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)GFM_ERR_TIMEOUT);
+                bail();
+                return;
+            }
+            // the next pass's first stages load during the rest of the iteration
+            if (threadIdx.x == 0) ring_prefetch(ring);
+        }
         if (work) {
-            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
-                mixed_op_group_hoisted<CH, U>(tab, sb, R.s1, R, cend, cur, P32, S32, be, ref, pin32, ts.rc[tank], Kt,
-                                              sh, accA[0]);
+            if constexpr (!STREAM)
+                for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
+                    mixed_op_group_hoisted<CH, U>(tab, sb, R.s1, R, cend, cur, P32, S32, be, ref, pin32, ts.rc[tank],
+                                                  Kt, sh, accA[0]);
             if (Kt > 0) {
                 // this CTA's share of the tank's cross faces
                 const int2 tr = ts.tcta[tank];
@@ -2005,7 +2083,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         }
         if (work && Kt > 0 && threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, ts.rc[tank], Kt, R.nw, sh.zb32);
         for (int k = 0; k < kTankCoarse; ++k) blkA[1 + k] = (work && k < Kt) ? (double)sh.zb32[k] : 0.0;
-        if (!batch_allreduce<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { batch_abort(a, bt); return; }
+        if (!batch_allreduce<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { bail(); return; }
         if (threadIdx.x < 32) {
             for (int t = threadIdx.x; t < T; t += 32) {
                 if (ts.act[t] != kGo) continue;
@@ -2058,7 +2136,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         }
         double blkB[2];
         block_sum_ff<2>(sh, accB, blkB);
-        if (!batch_allreduce<2>(g, sh, ts, bt, blkB)) { batch_abort(a, bt); return; }
+        if (!batch_allreduce<2>(g, sh, ts, bt, blkB)) { bail(); return; }
         { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
         if (threadIdx.x < 32) {
             bool any = false;
@@ -2089,7 +2167,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             // fold e into x and replace r by the true residual for the tanks
             // that asked (restarts also clear their direction)
             if (!batch_replace<CH>(a, bt, g, sh, ts, R, tank, cend, ref, pin64, cur, true, false)) {
-                batch_abort(a, bt);
+                bail();
                 return;
             }
             if (threadIdx.x < 32) {
@@ -2127,15 +2205,15 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             }
         }
         __syncthreads();
-        if (sh.flag) take_assignment();
+        if (sh.flag) take_assignment(true);
         __syncthreads();
     }
     // every tank gets CTAs again for the final residuals
     if (threadIdx.x == 0) batch_rebalance(ts, T, (int)gridDim.x, true);
     __syncthreads();
-    take_assignment();
+    take_assignment(false);
     // per-tank finish: true residual, solution in caller order, L1 residual
-    if (!grid_sync(g, sh)) { batch_abort(a, bt); return; }
+    if (!grid_sync(g, sh)) { bail(); return; }
     double v[2] = {0.0, 0.0};
     for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
         const int i = s * kSlice + R.lane;
@@ -2148,7 +2226,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         }
     }
     block_sum_f64<2>(sh, v);
-    if (!batch_allreduce<2>(g, sh, ts, bt, v)) { batch_abort(a, bt); return; }
+    if (!batch_allreduce<2>(g, sh, ts, bt, v)) { bail(); return; }
     if (threadIdx.x < 32) {
         for (int t = threadIdx.x; t < T; t += 32) {
             ts.xavg[t] = ts.tot[1][t] / (double)(a.n_per_tank ? a.n_per_tank[t] : 1);
@@ -2171,7 +2249,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         }
     }
     block_sum_f64<2>(sh, w);
-    if (!batch_allreduce<2>(g, sh, ts, bt, w)) { batch_abort(a, bt); return; }
+    if (!batch_allreduce<2>(g, sh, ts, bt, w)) { bail(); return; }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const int e = ld_volatile_i32(a.err);
         for (int t = threadIdx.x; t < T; t += 32) {
@@ -2189,9 +2267,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     }
 }
 
-const void *batched_kernel(int max_width)
+const void *batched_kernel(int max_width, bool streamed)
 {
-    return max_width <= 4 ? (const void *)k_solve_batched<4> : (const void *)k_solve_batched<8>;
+    if (max_width <= 4) return streamed ? (const void *)k_solve_batched<4, true> : (const void *)k_solve_batched<4, false>;
+    return streamed ? (const void *)k_solve_batched<8, true> : (const void *)k_solve_batched<8, false>;
 }
 
 // Instantiations by faces per row chunk (4 for 2D hex meshes, 8 otherwise)
