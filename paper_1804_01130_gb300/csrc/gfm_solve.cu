@@ -1559,6 +1559,9 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 // ---------------------------------------------------------------------------
 namespace {
 
+// Iterations between rounds of residual replacements while a tank waits for one.
+constexpr int kReplaceRound = 32;
+
 struct TankState {
     double bnorm[kMaxTanks], sc[kMaxTanks], isc[kMaxTanks], gam[kMaxTanks], gam_prev[kMaxTanks];
     double rho_max[kMaxTanks], best[kMaxTanks], rho_stop[kMaxTanks], xavg[kMaxTanks];
@@ -1582,9 +1585,13 @@ struct TankState {
     double y[kTankCoarse][kMaxTanks];
     float c32[kTankCoarse][kMaxTanks];
     int act[kMaxTanks];   // kGo while iterating, else kConverged / kNotConverged / kBreakdown
-    int flag[kMaxTanks];  // pending replacement: 0, kUpdate, kRestart, kNotConverged
+    int flag[kMaxTanks];  // replacement in this iteration: 0, kUpdate, kRestart, kNotConverged
+    // a replacement a tank asked for while it can still iterate (kUpdate):
+    // it waits for the next replacement round
+    int pend[kMaxTanks];
     int iters[kMaxTanks], updates[kMaxTanks], stall[kMaxTanks], last_upd[kMaxTanks], restarts[kMaxTanks];
     int any_flag, any_active;
+    int round_age;  // iterations since the last replacement round
 };
 
 // Per-tank all-reduce.  Every CTA writes its partials, and after the grid
@@ -1979,6 +1986,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             ts.rho_stop[t] = rtol2 * (bn * ts.sc[t]) * (bn * ts.sc[t]);
             ts.act[t] = kGo;
             ts.flag[t] = 0;
+            ts.pend[t] = 0;
             ts.iters[t] = ts.updates[t] = ts.stall[t] = ts.last_upd[t] = ts.restarts[t] = 0;
             ts.be[t] = 0.0f;
             ts.gam_prev[t] = 1.0;
@@ -2016,6 +2024,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        ts.round_age = 0;
         ts.n_active = T;  // re-plan as soon as any tank is done
         if constexpr (STREAM) ring_prefetch(ring);
     }
@@ -2138,11 +2147,20 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         block_sum_ff<2>(sh, accB, blkB);
         if (!batch_allreduce<2>(g, sh, ts, bt, blkB)) { bail(); return; }
         { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
+        // Replacements come in rounds: a tank that asks for one (its FP32
+        // residual fell a decade, claims convergence, or 1000 iterations
+        // passed) keeps iterating until the next round, which comes once
+        // every kReplaceRound iterations while any tank waits, or at once
+        // when a tank cannot go on (breakdown, iteration cap).  Every
+        // replacement holds all CTAs at its barriers, so serving many tanks
+        // at one of them costs the others far less; a wait of kReplaceRound
+        // iterations moves an FP32 residual by about a decade at most on
+        // these systems, well inside what FP32 resolves.
         if (threadIdx.x < 32) {
-            bool any = false;
+            bool now = false, waiting = false;
             for (int t = threadIdx.x; t < T; t += 32) {
                 if (ts.act[t] != kGo) continue;
-                if (ts.flag[t] == kRestart) { any = true; continue; }
+                if (ts.flag[t] == kRestart) { now = true; continue; }
                 const int it = ++ts.iters[t];
                 ts.gam_prev[t] = ts.gam[t];
                 const double gam = ts.tot[0][t], rho = ts.tot[1][t];
@@ -2150,17 +2168,33 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                 if (rho > ts.rho_max[t]) ts.rho_max[t] = rho;
                 if (it >= a.max_iters) {
                     ts.flag[t] = kNotConverged;
-                } else if (rho <= 1e-2 * ts.rho_max[t] || rho <= ts.rho_stop[t] || !(gam > 0.0) ||
-                           it - ts.last_upd[t] >= 1000) {
+                    now = true;
+                } else if (!(gam > 0.0)) {
                     ts.flag[t] = kUpdate;
                     ts.last_upd[t] = it;
+                    now = true;
                 } else {
+                    if (ts.pend[t] == 0 &&
+                        (rho <= 1e-2 * ts.rho_max[t] || rho <= ts.rho_stop[t] || it - ts.last_upd[t] >= 1000)) {
+                        ts.pend[t] = kUpdate;
+                        ts.last_upd[t] = it;
+                    }
                     ts.be[t] = (float)(gam / ts.gam_prev[t]);
                 }
-                any |= ts.flag[t] != 0;
+                waiting |= ts.pend[t] != 0;
             }
-            any = __any_sync(0xffffffffu, any);
-            if (threadIdx.x == 0) ts.any_flag = any;
+            now = __any_sync(0xffffffffu, now);
+            waiting = __any_sync(0xffffffffu, waiting);
+            if (threadIdx.x == 0) {
+                ++ts.round_age;
+                ts.any_flag = now || (waiting && ts.round_age >= kReplaceRound);
+            }
+            __syncwarp();
+            if (ts.any_flag) {
+                for (int t = threadIdx.x; t < T; t += 32)
+                    if (ts.act[t] == kGo && ts.flag[t] == 0) ts.flag[t] = ts.pend[t];
+                if (threadIdx.x == 0) ts.round_age = 0;
+            }
         }
         __syncthreads();
         if (ts.any_flag) {
@@ -2175,6 +2209,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                     const int f = ts.flag[t];
                     if (ts.act[t] != kGo || f == 0) continue;
                     ts.flag[t] = 0;
+                    ts.pend[t] = 0;
                     ++ts.updates[t];
                     const double rel2 = ts.tot[0][t] / (ts.bnorm[t] * ts.bnorm[t]);
                     if (rel2 <= rtol2) { ts.act[t] = kConverged; continue; }
