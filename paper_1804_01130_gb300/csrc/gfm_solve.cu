@@ -381,12 +381,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+// L2 policy for data a pass reads once: its lines go first when L2 needs
+// room, so the vectors that the neighbour gathers reuse stay resident.
+__device__ __forceinline__ unsigned long long l2_evict_first()
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
+                                          unsigned long long pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
 }
 
 struct Ring {
@@ -419,8 +430,10 @@ __device__ __forceinline__ void ring_issue(Ring &g, int r)
     float *val = reinterpret_cast<float *>(col + g.cap);
     mbar_arrive_expect_tx(bar, 2u * bytes);
     if (bytes != 0u) {
-        bulk_load(col, g.gcol + b, bytes, bar);
-        bulk_load(val, g.gval + b, bytes, bar);
+        // the tables stream through once per pass: evict-first in L2
+        const unsigned long long pol = l2_evict_first();
+        bulk_load(col, g.gcol + b, bytes, bar, pol);
+        bulk_load(val, g.gval + b, bytes, bar, pol);
     }
     ++g.issued;
 }
@@ -1218,8 +1231,8 @@ __device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_en
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (sb + u * R.nw < s_end && ii[u] < n) {
-            P32[ii[u]] = pn[u];
-            S32[ii[u]] = si[u];
+            __stcs(P32 + ii[u], pn[u]);  // read once, by the update pass
+            __stcs(S32 + ii[u], si[u]);
             ff_add(acc, pn[u] * si[u]);
             if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p
         }
@@ -1282,8 +1295,8 @@ __device__ __forceinline__ void mixed_op_group_hoisted(const TabT &tab, int sb, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (sb + u * R.nw < s_end && ii[u] < n) {
-            P32[ii[u]] = pn[u];
-            S32[ii[u]] = si[u];
+            __stcs(P32 + ii[u], pn[u]);  // read once, by the update pass
+            __stcs(S32 + ii[u], si[u]);
             ff_add(acc, pn[u] * si[u]);
             if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p
         }
@@ -1471,19 +1484,21 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             for (int u = 0; u < UB; ++u) {
                 ii[u] = (sb + u * R.nw) * kSlice + R.lane;
                 act[u] = sb + u * R.nw < R.s1 && ii[u] < n;
-                pi[u] = act[u] ? P32[ii[u]] : 0.f;
-                si[u] = act[u] ? S32[ii[u]] : 0.f;
-                ri[u] = act[u] ? R32[ii[u]] : 0.f;
-                ei[u] = act[u] ? E[ii[u]] : 0.f;
-                di[u] = act[u] ? dinv[ii[u]] : 0.f;
+                // streamed once per iteration: evict-first (the gathered
+                // (u, p) pairs are what L2 should keep)
+                pi[u] = act[u] ? __ldcs(P32 + ii[u]) : 0.f;
+                si[u] = act[u] ? __ldcs(S32 + ii[u]) : 0.f;
+                ri[u] = act[u] ? __ldcs(R32 + ii[u]) : 0.f;
+                ei[u] = act[u] ? __ldcs(E + ii[u]) : 0.f;
+                di[u] = act[u] ? __ldcs(dinv + ii[u]) : 0.f;
                 cm[u] = (act[u] && K > 0) ? (int)comp[ii[u]] : -1;
             }
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
                 if (act[u]) {
-                    E[ii[u]] = fmaf(al, pi[u], ei[u]);
+                    __stcs(E + ii[u], fmaf(al, pi[u], ei[u]));
                     const float rn = fmaf(-al, si[u], ri[u]);
-                    R32[ii[u]] = rn;
+                    __stcs(R32 + ii[u], rn);
                     float un = rn * di[u];
                     if (cm[u] >= 0) un += sh.c32[cm[u]];
                     nxt[ii[u]] = make_float2(un, pi[u]);
@@ -2119,18 +2134,18 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                 for (int u = 0; u < UB; ++u) {
                     ii[u] = (sb + u * R.nw) * kSlice + R.lane;
                     act[u] = sb + u * R.nw < R.s1 && ii[u] < cend;
-                    pi[u] = act[u] ? P32[ii[u]] : 0.f;
-                    si[u] = act[u] ? S32[ii[u]] : 0.f;
-                    ri[u] = act[u] ? R32[ii[u]] : 0.f;
-                    ei[u] = act[u] ? E[ii[u]] : 0.f;
-                    di[u] = act[u] ? dinv[ii[u]] : 0.f;
+                    pi[u] = act[u] ? __ldcs(P32 + ii[u]) : 0.f;
+                    si[u] = act[u] ? __ldcs(S32 + ii[u]) : 0.f;
+                    ri[u] = act[u] ? __ldcs(R32 + ii[u]) : 0.f;
+                    ei[u] = act[u] ? __ldcs(E + ii[u]) : 0.f;
+                    di[u] = act[u] ? __ldcs(dinv + ii[u]) : 0.f;
                 }
 #pragma unroll
                 for (int u = 0; u < UB; ++u) {
                     if (act[u]) {
-                        E[ii[u]] = fmaf(al, pi[u], ei[u]);
+                        __stcs(E + ii[u], fmaf(al, pi[u], ei[u]));
                         const float rn = fmaf(-al, si[u], ri[u]);
-                        R32[ii[u]] = rn;
+                        __stcs(R32 + ii[u], rn);
                         float un = rn * di[u];
                         if (Kt > 0) {
                             const int cm = a.comp[ii[u]];
