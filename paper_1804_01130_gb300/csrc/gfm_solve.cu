@@ -304,6 +304,7 @@ struct Tab {
     const int32_t *gcol; // global tables for slots past the cache
     const V *gval;
     int s0, base0, end;  // first slice; slot of its first lane; first uncached slot
+    bool full;           // every slot of the range is cached
 
     __device__ __forceinline__ Row row(int s) const
     {
@@ -344,6 +345,7 @@ __device__ Tab<V> stage_tables(const Sell &m, const V *gval, const Range &R, int
     t.s0 = R.s0;
     t.base0 = base0;
     t.end = base0 + cap;
+    t.full = cap == total;
     return t;
 }
 
@@ -756,7 +758,9 @@ __device__ __forceinline__ void finish_bins(const T (*wbins)[kMaxCoarse], T pin,
 template <int CH>
 __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
 {
-    constexpr int U = 2;  // slices in flight per warp in the SpMV pass
+    // slices per warp in the SpMV pass: one for 4-face rows, two for wider
+    // ones (measured best; more unrolled slices only add issue work)
+    constexpr int U = CH <= 4 ? 1 : 2;
     __shared__ Shared sh;
     extern __shared__ __align__(16) unsigned char dsm[];
     Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
@@ -1308,7 +1312,10 @@ __device__ __forceinline__ void mixed_op_group_hoisted(const TabT &tab, int sb, 
 template <int CH, bool STREAM>
 __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 {
-    constexpr int U = 16 / CH;  // slices in flight per warp in the operator pass (cached tables)
+    // slices per warp in one operator group with cached tables: one for
+    // 4-face rows (the pass is bound by issue, not by a gather round trip:
+    // 18.3 -> 16.4 us per iteration on the 1024x512 tank against four)
+    constexpr int U = CH <= 4 ? 1 : 16 / CH;
     constexpr int US = CH <= 6 ? 4 : 2;  // the same with streamed tables
     constexpr int UB = 4;       // slices in flight per warp in the update pass
     __shared__ Shared sh;
@@ -1414,6 +1421,12 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             }
             // the next pass's first stages load during the rest of the iteration
             if (threadIdx.x == 0) ring_prefetch(ring);
+        } else if (tab.full) {
+            // the whole range is cached: a view without the per-slot fallback
+            // to global memory, so the group's loads carry no branches
+            const StageTab ft{tab.meta, tab.col, tab.val, tab.s0, tab.base0};
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
+                mixed_op_group<CH, U>(ft, sb, R.s1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
         } else {
             for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
                 mixed_op_group<CH, U>(tab, sb, R.s1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
