@@ -98,6 +98,7 @@ struct Shared {
     double zpin64;
     double Einv[kMaxCoarse * kMaxCoarse];  // staged copy of the coarse inverse
     int flag;
+    int flag2;  // a reduction's error check, published with its sums
     int ring_fail;  // a streamed-table stage did not arrive within the budget
 };
 
@@ -111,28 +112,38 @@ struct Grid {
     int parity;
 };
 
+// Thread 0: arrive at the grid barrier and wait for the other CTAs.  Each
+// poll reads the counter and the clock (a register, not a memory access);
+// the error flag, a second L2 round trip, only every 16th poll.  Returns
+// false on a timeout (recorded) or an error seen while waiting.
+__device__ __forceinline__ bool grid_arrive_wait(Grid &g)
+{
+    red_release_add_u32(g.bar, 1u);
+    const unsigned target = g.epoch * (unsigned)g.G;
+    unsigned long long t0 = 0;
+    for (unsigned k = 0;; ++k) {
+        const unsigned v = ld_acquire_u32(g.bar);
+        if ((int)(v - target) >= 0) break;
+        const unsigned long long now = gtime();
+        if (k == 0) t0 = now;
+        else if (now - t0 > g.budget) {
+            atomicCAS(g.err, 0, (int)GFM_ERR_TIMEOUT);
+            return false;
+        }
+        if ((k & 15u) == 15u && ld_volatile_i32(g.err) != 0) return false;
+    }
+    __threadfence();
+    return true;
+}
+
 // Grid-wide barrier.  Returns false if the solve must stop (a timeout here or
-// an error recorded by any CTA).
+// an error recorded by any CTA before the barrier completed).
 __device__ __forceinline__ bool grid_sync(Grid &g, Shared &sh)
 {
     __syncthreads();
     g.epoch += 1u;
     if (threadIdx.x == 0) {
-        int fail = 0;
-        red_release_add_u32(g.bar, 1u);
-        const unsigned target = g.epoch * (unsigned)g.G;
-        const unsigned long long t0 = gtime();
-        for (;;) {
-            const unsigned v = ld_acquire_u32(g.bar);
-            if ((int)(v - target) >= 0) break;
-            if (ld_volatile_i32(g.err) != 0) { fail = 1; break; }
-            if (gtime() - t0 > g.budget) {
-                atomicCAS(g.err, 0, (int)GFM_ERR_TIMEOUT);
-                fail = 1;
-                break;
-            }
-        }
-        __threadfence();
+        int fail = grid_arrive_wait(g) ? 0 : 1;
         if (!fail && ld_volatile_i32(g.err) != 0) fail = 1;
         sh.flag = fail;
     }
@@ -148,12 +159,21 @@ template <int NR>
 __device__ __forceinline__ bool grid_allreduce(Grid &g, Shared &sh, const double (&blk)[NR], double (&out)[NR],
                                                int nr = NR)
 {
+    int e = 0;
+    __syncthreads();
+    g.epoch += 1u;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NR; ++k)
             if (k < nr) g.partials[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
+        const bool ok = grid_arrive_wait(g);
+        // an error raised before the last arrival: read while the sums are
+        // read, checked with them
+        e = ok ? ld_volatile_i32(g.err) : 1;
+        sh.flag = ok ? 0 : 1;
     }
-    if (!grid_sync(g, sh)) return false;
+    __syncthreads();
+    if (sh.flag != 0) return false;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = warp; k < nr; k += nw) {
         const double *src = g.partials + ((size_t)g.parity * kMaxNR + k) * g.G;
@@ -169,8 +189,10 @@ __device__ __forceinline__ bool grid_allreduce(Grid &g, Shared &sh, const double
         for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if (lane == 0) sh.out[k] = acc;
     }
+    if (threadIdx.x == 0) sh.flag2 = e;
     g.parity ^= 1;
     __syncthreads();
+    if (sh.flag2 != 0) return false;
 #pragma unroll
     for (int k = 0; k < NR; ++k) out[k] = (k < nr) ? sh.out[k] : 0.0;
     return true;
