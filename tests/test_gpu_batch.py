@@ -82,6 +82,25 @@ def test_batched_converged_tank_drops_out():
     assert all(i.status == 0 and i.iters > 0 for i in infos[1:])
 
 
+def test_batched_solve_is_bit_reproducible():
+    """The device re-plans the tank->CTA table as tanks finish and serves
+    residual replacements in rounds; both are decided from sums every CTA
+    computes in the same order, so a repeated solve (and a re-assembly)
+    gives the same bits and the same iteration counts."""
+    tanks = _tanks()
+    b = _g().GFMBatch(tanks)
+    runs = []
+    for rep in range(3):
+        if rep != 1:  # re-assemble before the first and the last solve
+            b.assemble(_cat(tanks, "alpha"), _cat(tanks, "phi"), _phys(tanks))
+        p, _, infos = b.solve(rtol=1e-11)
+        runs.append((p.clone(), [(i.iters, i.refinements) for i in infos]))
+    assert len(set(it for it, _ in runs[0][1])) > 1  # tanks finished at different times
+    for p, its in runs[1:]:
+        assert torch.equal(p, runs[0][0])
+        assert its == runs[0][1]
+
+
 def test_batched_solve_in_cuda_graph():
     tanks = _tanks()
     g = _g()
