@@ -55,10 +55,11 @@ bool plan_batch_ctas(const BatchTables &bt, int grid, std::vector<int32_t> &cta4
                      std::string &err, const std::vector<double> &weight = {});
 
 // Most slices one CTA can hold after the batched solve re-plans its CTA
-// table on the device.  A re-plan over a set S of tanks gives tank t
-// 1 + floor((grid - |S|) sl_t / sl_S) CTAs or one more (sl: slices), and a
-// CTA ceil(sl_t / CTAs) slices; (grid - |S|) / sl_S only grows as S shrinks,
-// so the plan over all tanks bounds every re-plan.
+// table on the device: an upper bound, the split over all tanks that gives
+// tank t 1 + floor((grid - T) sl_t / sl_all) CTAs (sl: slices).  A device
+// re-plan over a set S of tanks minimises the most slices per CTA over S;
+// that minimum is at most the one over all tanks, which is at most this
+// split's.
 int batch_replan_max_slices(const BatchTables &bt, int grid);
 
 }  // namespace gfm

@@ -1789,54 +1789,77 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
     return grid_sync(g, sh);  // u complete before it is gathered
 }
 
-// Thread 0 of every CTA: split the grid among the tanks that still iterate
-// (all tanks when `all`): each gets one CTA plus a share of the rest in
-// proportion to its slices (largest remainders first, ties to the lower
-// tank); tanks left out get no CTA.  A pure function of the active set,
-// which every CTA holds, so every CTA builds the same table.
+// Warp 0 of every CTA: split the grid among the tanks that take part (those
+// still iterating, or all of them with `all`).  Each gets one CTA, then the
+// CTAs go one at a time to the tank whose CTAs hold the most slices each
+// (ties to the lower tank), which minimises the most slices any CTA holds:
+// every tank iterates once per grid step, so the step lasts as long as the
+// busiest CTA.  Lane l keeps tanks l, l + 32, ...; each step is a warp
+// argmax.  A pure function of state every CTA holds, so every CTA builds the
+// same table.
 __device__ void batch_rebalance(TankState &ts, int T, int G, bool all)
 {
-    long long total = 0;
+    constexpr int PT = kMaxTanks / 32;  // tanks per lane
+    const int lane = threadIdx.x & 31;
+    int g[PT];
+    long long sl[PT];
     int nact = 0;
-    for (int t = 0; t < T; ++t)
-        if (all || ts.act[t] == kGo) {
-            total += ts.nslc[t];
-            ++nact;
-        }
-    if (nact == 0) return;
-    if (total <= 0) total = 1;
-    const long long extra = G - nact;
-    bool got[kMaxTanks];
-    int given = 0;
-    for (int t = 0; t < T; ++t) {
-        const bool on = all || ts.act[t] == kGo;
-        const int g = on ? 1 + (int)((extra * ts.nslc[t]) / total) : 0;
-        ts.tcta[t] = make_int2(0, g);  // .y holds the count for now
-        got[t] = !on;
-        given += g;
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int t = lane + 32 * j;
+        const bool on = t < T && (all || ts.act[t] == kGo);
+        g[j] = on ? 1 : 0;
+        sl[j] = on ? ts.nslc[t] : 0;
+        nact += on ? 1 : 0;
     }
-    for (int left = G - given; left > 0; --left) {  // one more to the largest remainders
-        int best = -1;
-        long long bestr = -1;
-        for (int t = 0; t < T; ++t) {
-            if (got[t]) continue;
-            const long long r = (extra * ts.nslc[t]) % total;
-            if (r > bestr) {
-                bestr = r;
-                best = t;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) nact += __shfl_xor_sync(0xffffffffu, nact, off);
+    if (nact == 0) return;
+    for (int left = G - nact; left > 0; --left) {
+        // this lane's busiest tank (slices per CTA as the fraction bn / bd)
+        long long bn = -1;
+        int bd = 1, bt = 0x7fffffff;
+#pragma unroll
+        for (int j = 0; j < PT; ++j)
+            if (g[j] > 0 && sl[j] * bd > bn * g[j]) {
+                bn = sl[j];
+                bd = g[j];
+                bt = lane + 32 * j;
+            }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const long long on = __shfl_xor_sync(0xffffffffu, bn, off);
+            const int od = __shfl_xor_sync(0xffffffffu, bd, off);
+            const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+            const long long a = on * bd, b = bn * od;
+            if (a > b || (a == b && ot < bt)) {
+                bn = on;
+                bd = od;
+                bt = ot;
             }
         }
-        if (best < 0) break;
-        got[best] = true;
-        ts.tcta[best].y += 1;
+        if ((bt & 31) == lane) {
+#pragma unroll
+            for (int j = 0; j < PT; ++j)
+                if (j == (bt >> 5)) g[j] += 1;
+        }
     }
-    int c = 0;
-    for (int t = 0; t < T; ++t) {
-        const int g = ts.tcta[t].y;
-        ts.tcta[t] = make_int2(c, c + g);
-        c += g;
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int t = lane + 32 * j;
+        if (t < T) ts.tcta[t] = make_int2(0, g[j]);  // .y holds the count for now
     }
-    list_wide(ts, T);
+    __syncwarp();
+    if (lane == 0) {
+        int c = 0;
+        for (int t = 0; t < T; ++t) {
+            const int n = ts.tcta[t].y;
+            ts.tcta[t] = make_int2(c, c + n);
+            c += n;
+        }
+        list_wide(ts, T);
+    }
+    __syncwarp();
 }
 
 // Slice tables of the batched solve, staged in shared memory like the
@@ -2284,17 +2307,16 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             for (int t = 0; t < T; ++t) nact += ts.act[t] == kGo;
             ts.any_active = nact > 0;
             sh.flag = (nact > 0 && nact < ts.n_active);  // tanks finished: re-plan
-            if (sh.flag) {
-                ts.n_active = nact;
-                batch_rebalance(ts, T, (int)gridDim.x, false);
-            }
+            if (sh.flag) ts.n_active = nact;
         }
+        __syncwarp();
+        if (threadIdx.x < 32 && sh.flag) batch_rebalance(ts, T, (int)gridDim.x, false);
         __syncthreads();
         if (sh.flag) take_assignment(true);
         __syncthreads();
     }
     // every tank gets CTAs again for the final residuals
-    if (threadIdx.x == 0) batch_rebalance(ts, T, (int)gridDim.x, true);
+    if (threadIdx.x < 32) batch_rebalance(ts, T, (int)gridDim.x, true);
     __syncthreads();
     take_assignment(false);
     // per-tank finish: true residual, solution in caller order, L1 residual
