@@ -1656,11 +1656,18 @@ __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &
                                                 const double (&blk)[NR])
 {
     static_assert(NR <= kBatchNR, "batched reduction buffer too small");
+    int e = 0;
+    __syncthreads();
+    g.epoch += 1u;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NR; ++k) g.partials[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
+        const bool ok = grid_arrive_wait(g);
+        e = ok ? ld_volatile_i32(g.err) : 1;  // checked with the sums, as in grid_allreduce
+        sh.flag = ok ? 0 : 1;
     }
-    if (!grid_sync(g, sh)) return false;
+    __syncthreads();
+    if (sh.flag != 0) return false;
     const int G = g.G, T = bt.T;
     double *red = ts.red;
     const double *src = g.partials + (size_t)g.parity * kMaxNR * G;
@@ -1684,9 +1691,10 @@ __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) ts.tot[k][t] = acc;
     }
+    if (threadIdx.x == 0) sh.flag2 = e;
     g.parity ^= 1;
     __syncthreads();
-    return true;
+    return sh.flag2 == 0;
 }
 
 // Thread 0: list the tanks whose CTA count calls for a warp-wide sum.
