@@ -180,12 +180,16 @@ gfm_status gfm_create(const gfm_mesh *mesh, int32_t renumber, gfm_stream stream,
  * order; gfm_assemble's `phys` is then a host array of n_tanks entries, each
  * ref_cell numbered within its tank and >= 0.  gfm_solve runs GFM_MIXED only:
  * every tank keeps its own CG scalars, residual replacements and stopping
- * test, finished tanks drop out while the others iterate, and `info` points
- * to n_tanks records (the returned status is the last failing tank's).  The
- * launch needs at least one CTA per tank.  The adjoint and the host-buffer
- * entry point take single-mesh handles.  Each tank gets its own coarse space
- * (up to its 2 largest one-phase regions, see gfm_set_coarse), so tanks
- * iterate as a single mesh would.  Errors as gfm_create.
+ * test, and `info` points to n_tanks records (the returned status is the
+ * last failing tank's).  The launch needs at least one CTA per tank.  When
+ * tanks finish, their CTAs are handed to the tanks still iterating.  A tank
+ * that asks for an FP64 residual replacement keeps iterating in FP32 until
+ * the next replacement round (at most 32 iterations later), so its iteration
+ * count can run a little above a single-mesh solve's.  Results are
+ * bit-reproducible from run to run.  The adjoint and the host-buffer entry
+ * point take single-mesh handles.  Each tank gets its own coarse space (up
+ * to its 2 largest one-phase regions, see gfm_set_coarse).  Errors as
+ * gfm_create.
  */
 gfm_status gfm_create_batched(const gfm_mesh *meshes, int32_t n_tanks, int32_t renumber, gfm_stream stream,
                               gfm_handle *out);

@@ -1601,11 +1601,12 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 
 // ---------------------------------------------------------------------------
 // Batched mixed-precision solve: many independent tanks in one persistent
-// launch.  Every CTA works on one tank; per-tank scalars live in shared memory
-// and every CTA computes ALL tanks' sums and decisions from the same partials,
-// so all CTAs agree on the barrier schedule: a residual replacement runs (for
-// the tanks that need it) whenever any tank needs one, and finished tanks drop
-// out of the passes while the others iterate.
+// launch.  Every CTA works on one tank at a time; per-tank scalars live in
+// shared memory and every CTA computes ALL tanks' sums and decisions from the
+// same partials, so all CTAs agree on the barrier schedule without talking:
+// each grid step is one iteration of every tank still iterating, residual
+// replacements are served in rounds for the tanks that asked, and when tanks
+// finish every CTA re-plans the tank->CTA table over the rest.
 // ---------------------------------------------------------------------------
 namespace {
 
