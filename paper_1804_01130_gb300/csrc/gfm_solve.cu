@@ -1640,6 +1640,8 @@ struct TankState {
     // a replacement a tank asked for while it can still iterate (kUpdate):
     // it waits for the next replacement round
     int pend[kMaxTanks];
+    int wait[kMaxTanks];      // 1: the tank idles until the next replacement round
+    int last_rep[kMaxTanks];  // iteration of the tank's last residual replacement
     int iters[kMaxTanks], updates[kMaxTanks], stall[kMaxTanks], last_upd[kMaxTanks], restarts[kMaxTanks];
     int any_flag, any_active;
     int round_age;  // iterations since the last replacement round
@@ -2069,6 +2071,8 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             ts.act[t] = kGo;
             ts.flag[t] = 0;
             ts.pend[t] = 0;
+            ts.wait[t] = 0;
+            ts.last_rep[t] = 0;
             ts.iters[t] = ts.updates[t] = ts.stall[t] = ts.last_upd[t] = ts.restarts[t] = 0;
             ts.be[t] = 0.0f;
             ts.gam_prev[t] = 1.0;
@@ -2112,7 +2116,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     }
     __syncthreads();
     while (ts.any_active) {
-        const bool work = ts.act[tank] == kGo;
+        const bool work = ts.act[tank] == kGo && ts.wait[tank] == 0;
         const float be = ts.be[tank];
         // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s,
         // and the tank's Z^T (A p) from its faces between coarse regions
@@ -2177,7 +2181,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         if (!batch_allreduce<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { bail(); return; }
         if (threadIdx.x < 32) {
             for (int t = threadIdx.x; t < T; t += 32) {
-                if (ts.act[t] != kGo) continue;
+                if (ts.act[t] != kGo || ts.wait[t]) continue;
                 const double ps = ts.tot[0][t];
                 const bool ok = ps > 0.0 && isfinite(ps) && ts.gam[t] > 0.0;
                 ts.al[t] = ok ? (float)(ts.gam[t] / ps) : 0.0f;
@@ -2224,24 +2228,37 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                     }
                 }
             }
+        } else if (ts.act[tank] == kGo && ts.wait[tank]) {
+            // an idle tank keeps its (u, p) pairs across the buffer swap
+            for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+                const int i = s * kSlice + R.lane;
+                if (i < cend) nxt[i] = cur[i];
+            }
         }
         double blkB[2];
         block_sum_ff<2>(sh, accB, blkB);
         if (!batch_allreduce<2>(g, sh, ts, bt, blkB)) { bail(); return; }
         { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
-        // Replacements come in rounds: a tank that asks for one (its FP32
-        // residual fell a decade, claims convergence, or 1000 iterations
-        // passed) keeps iterating until the next round, which comes once
-        // every kReplaceRound iterations while any tank waits, or at once
-        // when a tank cannot go on (breakdown, iteration cap).  Every
+        // Replacements come in rounds.  A tank that asks for one because its
+        // FP32 residual fell a decade or 1000 iterations passed keeps
+        // iterating until the next round, which comes once every
+        // kReplaceRound iterations while any tank waits.  A tank whose FP32
+        // residual claims convergence, or fell its decade within two rounds
+        // of its last replacement, stops and idles until then: its FP32
+        // recurrence would run on past convergence (a tank of a few dozen
+        // cells does in a handful of iterations) and the direction kept
+        // through the replacement would be noise, which stalls the
+        // refinement.  The round comes at once when a tank cannot go on
+        // (breakdown, iteration cap) or no tank is left iterating.  Every
         // replacement holds all CTAs at its barriers, so serving many tanks
         // at one of them costs the others far less; a wait of kReplaceRound
         // iterations moves an FP32 residual by about a decade at most on
         // these systems, well inside what FP32 resolves.
         if (threadIdx.x < 32) {
-            bool now = false, waiting = false;
+            bool now = false, waiting = false, going = false;
             for (int t = threadIdx.x; t < T; t += 32) {
                 if (ts.act[t] != kGo) continue;
+                if (ts.wait[t]) { waiting = true; continue; }
                 if (ts.flag[t] == kRestart) { now = true; continue; }
                 const int it = ++ts.iters[t];
                 ts.gam_prev[t] = ts.gam[t];
@@ -2255,16 +2272,25 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                     ts.flag[t] = kUpdate;
                     ts.last_upd[t] = it;
                     now = true;
+                } else if (rho <= ts.rho_stop[t]) {
+                    ts.pend[t] = kUpdate;
+                    ts.wait[t] = 1;
+                    ts.last_upd[t] = it;
                 } else {
-                    if (ts.pend[t] == 0 &&
-                        (rho <= 1e-2 * ts.rho_max[t] || rho <= ts.rho_stop[t] || it - ts.last_upd[t] >= 1000)) {
+                    if (ts.pend[t] == 0 && (rho <= 1e-2 * ts.rho_max[t] || it - ts.last_upd[t] >= 1000)) {
                         ts.pend[t] = kUpdate;
                         ts.last_upd[t] = it;
+                        if (it - ts.last_rep[t] < 2 * kReplaceRound) ts.wait[t] = 1;
                     }
-                    ts.be[t] = (float)(gam / ts.gam_prev[t]);
+                    if (ts.wait[t] == 0) {
+                        ts.be[t] = (float)(gam / ts.gam_prev[t]);
+                        going = true;
+                    }
                 }
                 waiting |= ts.pend[t] != 0;
             }
+            going = __any_sync(0xffffffffu, going);
+            now = now || (waiting && !going);
             now = __any_sync(0xffffffffu, now);
             waiting = __any_sync(0xffffffffu, waiting);
             if (threadIdx.x == 0) {
@@ -2292,6 +2318,8 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                     if (ts.act[t] != kGo || f == 0) continue;
                     ts.flag[t] = 0;
                     ts.pend[t] = 0;
+                    ts.wait[t] = 0;
+                    ts.last_rep[t] = ts.iters[t];
                     ++ts.updates[t];
                     const double rel2 = ts.tot[0][t] / (ts.bnorm[t] * ts.bnorm[t]);
                     if (rel2 <= rtol2) { ts.act[t] = kConverged; continue; }

@@ -101,6 +101,46 @@ def test_batched_solve_is_bit_reproducible():
         assert its == runs[0][1]
 
 
+def test_batched_128_tanks_at_the_limit():
+    """The most tanks a batch takes (128): the device re-plans the CTA table
+    over tanks 0..127 (each lane of the planning warp holds four), every
+    tank meets its tolerance and matches the oracle."""
+    g = _g()
+    tanks = [cases.box_case(6 + (k % 7), 4 + (k % 5), 1, seed=500 + k, ka=0.02 + 0.001 * k, nwaves=1 + k % 3)
+             for k in range(128)]
+    b = g.GFMBatch(tanks)
+    b.assemble(_cat(tanks, "alpha"), _cat(tanks, "phi"), _phys(tanks))
+    p, _, infos = b.solve(rtol=1e-11)
+    pn = p.cpu().numpy()
+    c0 = 0
+    for t, inf in zip(tanks, infos):
+        assert inf.status == 0 and inf.rel_res_l2 <= 1e-11, inf
+        p_ref, _, _, _ = oracle.solve(t, direct=True)
+        assert np.linalg.norm(pn[c0:c0 + t.n] - p_ref) <= 1e-6 * np.linalg.norm(p_ref)
+        c0 += t.n
+    with pytest.raises(g.GFMError):
+        g.GFMBatch(tanks + tanks[:1])  # 129 tanks
+
+
+def test_batched_single_tank_matches_single_mesh():
+    """A batch of one tank is the single-mesh problem: same assembly bits,
+    solution within the mixed tolerance of the single-mesh solve."""
+    g = _g()
+    t = cases.box_case(48, 24, 1, seed=77, ka=0.1, nwaves=2)
+    b = g.GFMBatch([t])
+    b.assemble(_cat([t], "alpha"), _cat([t], "phi"), _phys([t]))
+    s = g.GFM.from_case(t, renumber=1)
+    s.assemble(torch.as_tensor(t.alpha), torch.as_tensor(t.phi), t.rho_w, t.rho_a, t.g, t.ref_cell, t.ref_value)
+    eb = {k: v.cpu().numpy() for k, v in b.export_system().items()}
+    es = {k: v.cpu().numpy() for k, v in s.export_system().items()}
+    for k in ("gamma", "jump", "diag", "b"):
+        assert np.array_equal(eb[k], es[k]), k
+    pb, _, infos = b.solve(rtol=1e-11)
+    ps, _, info = s.solve(mode="mixed", rtol=1e-11)
+    assert infos[0].status == 0 and info.status == 0
+    assert float(torch.linalg.norm(pb - ps) / torch.linalg.norm(ps)) <= 1e-8
+
+
 def test_batched_solve_in_cuda_graph():
     tanks = _tanks()
     g = _g()
