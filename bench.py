@@ -20,8 +20,9 @@ All use rho_w = 1000, rho_a = 1, g = (0, -9.81, 0), one pinned cell per mesh.
 A step = one pass of the hot path on device-resident inputs: assemble the
 GFM system (interface fraction, face coefficients, jump source, cell sums),
 solve it with the mixed-precision persistent solver (FP32 inner PCG inside
-FP64 reliable updates, two-level preconditioner on single meshes), and, on
-single meshes, compute the corrected face flux.  The L2 is flushed (a 512
+FP64 reliable updates, two-level preconditioner: up to 8 one-phase regions on
+a single mesh, the 2 largest of each tank in a batch), and, on single
+meshes, compute the corrected face flux.  The L2 is flushed (a 512
 MiB write) before every step.
 
 Metric: cell-iterations per second (sum over meshes of cells x CG
