@@ -261,7 +261,18 @@ class SingleMesh:
         import torch
         out = {}
         p_mixed = self.p.detach().cpu().numpy()
-        self.h.assemble(self.alpha, self.phi, **self.phys)
+        # assembly alone (faces, cells, coarse space), after an L2 flush, off
+        # the timed region; the last one leaves the system for the FP64 solves
+        asm_ms = []
+        for i in range(3):
+            flush.fill_(float(10 + i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            self.h.assemble(self.alpha, self.phi, **self.phys)
+            b.record(stream)
+            torch.cuda.synchronize()
+            asm_ms.append(a.elapsed_time(b))
+        out["assembly_ms"] = statistics.mean(asm_ms)
         fp64_ms = []
         for i in range(2):
             flush.fill_(float(i))
@@ -559,7 +570,8 @@ def run_gfm(args, rank, local, world):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (trec["dram_bytes_per_launch"] if trec else None),
             "kernel": "k_solve_batched" if key == "batch64" else "k_solve_mixed", "kernel_ms": kms,
-            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg,
+            "peak_kind": peak_kind, "frac_of_spec_8000_gbs": achieved / 8000.0,
+            "algorithmic_bytes_per_launch": bytes_alg,
             "bytes_model": "(52 + 12 F/n) B per cell-iteration + (24 + 16 F/n) B per cell per FP64 replacement"}
     if key == "tank2d":
         roof["note"] = "the tank's FP32 working set (~35 MB) stays in L2 across iterations"
