@@ -1984,6 +1984,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             ts.tend[t] = bt.cta[r.x].w;
         }
     }
+    __syncwarp();  // thread 0 reads what the other lanes of warp 0 wrote
     if (threadIdx.x == 0) {
         ts.red = reinterpret_cast<double *>(dsm);
         list_wide(ts, T);
