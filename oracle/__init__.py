@@ -23,7 +23,8 @@ _SRC = os.path.join(_HERE, "gfm_oracle.c")
 _LIB = os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
 _lib = None
 
-MUT_NONE, MUT_JUMP_SIGN_EQ15, MUT_LAMBDA_FROM_OWNER, MUT_ARITH_BETA, MUT_DROP_JUMP, MUT_SWAP_ALPHA_DERIV = range(6)
+(MUT_NONE, MUT_JUMP_SIGN_EQ15, MUT_LAMBDA_FROM_OWNER, MUT_ARITH_BETA, MUT_DROP_JUMP, MUT_SWAP_ALPHA_DERIV,
+ MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ) = range(8)
 KIND_DRY, KIND_WET, KIND_IF_OWNER_WET, KIND_IF_OWNER_DRY = range(4)
 
 
@@ -52,7 +53,7 @@ def _load():
         lib.gfm_oracle_spmv.restype = None
         lib.gfm_oracle_pcg.argtypes = [I, P, P, P, P, P, D, I, ct.POINTER(I), ct.POINTER(D)]
         lib.gfm_oracle_pcg.restype = I
-        lib.gfm_oracle_pcg_fixed.argtypes = [I, P, P, P, P, P, I]
+        lib.gfm_oracle_pcg_fixed.argtypes = [I, P, P, P, P, P, I, I]
         lib.gfm_oracle_pcg_fixed.restype = D
         lib.gfm_oracle_cholesky_solve.argtypes = [I, P, P, P, P, P]
         lib.gfm_oracle_cholesky_solve.restype = I
@@ -173,12 +174,14 @@ def pcg(sys_: System, b=None, x0=None, rtol: float = 1e-13, maxit: int = 200000)
     return x, it.value, rel.value, st
 
 
-def pcg_fixed(sys_: System, iters: int, b=None) -> float:
-    """Exactly ``iters`` Jacobi-PCG iterations from x = 0 (for timing)."""
+def pcg_fixed(sys_: System, iters: int, b=None, x0=None, mutate: int = MUT_NONE):
+    """Exactly ``iters`` Jacobi-PCG iterations, no convergence test (timing
+    samples).  Returns (x_k, ||r_k||_2 of the recurrence residual)."""
     b = _f64(sys_.b if b is None else b)
-    x = np.zeros(sys_.n)
-    return float(_load().gfm_oracle_pcg_fixed(sys_.n, _p(sys_.rowptr), _p(sys_.col), _p(sys_.val), _p(b), _p(x),
-                                              int(iters)))
+    x = np.zeros(sys_.n) if x0 is None else _f64(x0).copy()
+    rr = float(_load().gfm_oracle_pcg_fixed(sys_.n, _p(sys_.rowptr), _p(sys_.col), _p(sys_.val), _p(b), _p(x),
+                                            int(iters), int(mutate)))
+    return x, rr
 
 
 def cholesky_solve(sys_: System, b=None) -> np.ndarray:

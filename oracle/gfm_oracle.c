@@ -54,6 +54,8 @@
 #define MUT_ARITH_BETA 3        /* arithmetic mean of beta instead of Eq. 18   */
 #define MUT_DROP_JUMP 4         /* drop the jump source                        */
 #define MUT_SWAP_ALPHA_DERIV 5  /* swap d lambda/d alpha_W and d alpha_D        */
+#define MUT_PCG_NO_PRECOND 6    /* fixed-count PCG: drop the Jacobi weights      */
+#define MUT_PCG_STALE_RZ 7      /* fixed-count PCG: never update r.z             */
 
 int gfm_oracle_version(void) { return 3; }
 
@@ -292,10 +294,16 @@ done:
 
 /*
  * Fixed-count Jacobi-PCG iterations, for timing the oracle on a bounded
- * sample: exactly `iters` iterations from x, no convergence test.
+ * sample: exactly `iters` iterations of the same textbook recurrence as
+ * gfm_oracle_pcg (M = diag(A)) from the x passed in, no convergence test and
+ * no restart.  x is overwritten with the k-th iterate; returns ||r_k||_2 of
+ * the recurrence residual.  In exact arithmetic the k-th iterate minimises
+ * the A-norm of the error over x0 + K_k(M^-1 A, M^-1 r0), the property the
+ * CPU tests check it against.  `mutate` plants a mistake for those tests
+ * (0 = faithful).
  */
 double gfm_oracle_pcg_fixed(int n, const int64_t *rowptr, const int32_t *col, const double *val,
-                            const double *b, double *x, int iters)
+                            const double *b, double *x, int iters, int mutate)
 {
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
     double *z = (double *)malloc(sizeof(double) * (size_t)n);
@@ -306,7 +314,7 @@ double gfm_oracle_pcg_fixed(int n, const int64_t *rowptr, const int32_t *col, co
     for (int i = 0; i < n; ++i) {
         double d = 0.0;
         for (int64_t a = rowptr[i]; a < rowptr[i + 1]; ++a) if (col[a] == i) d = val[a];
-        dinv[i] = 1.0 / d;
+        dinv[i] = (mutate == MUT_PCG_NO_PRECOND) ? 1.0 : 1.0 / d;
     }
     gfm_oracle_spmv(n, rowptr, col, val, x, q);
     for (int i = 0; i < n; ++i) { r[i] = b[i] - q[i]; z[i] = dinv[i] * r[i]; p[i] = z[i]; }
@@ -319,7 +327,7 @@ double gfm_oracle_pcg_fixed(int n, const int64_t *rowptr, const int32_t *col, co
         for (int i = 0; i < n; ++i) { x[i] += a * p[i]; r[i] -= a * q[i]; z[i] = dinv[i] * r[i]; }
         double rz2 = dot(n, r, z);
         double be = (rz != 0.0) ? rz2 / rz : 0.0;
-        rz = rz2;
+        if (mutate != MUT_PCG_STALE_RZ) rz = rz2;
 #pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) p[i] = z[i] + be * p[i];
     }
