@@ -269,7 +269,11 @@ gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *
  * Solves A x = b by FP64 Jacobi-preconditioned CG for a symmetric positive
  * definite A in CSR form, all DEVICE pointers owned by the caller:
  *   row_ptr [n+1], col [nnz], val [nnz] (int32, int32, FP64); every row
- *   holds a positive diagonal entry.  The GFM system of gfm_assemble is
+ *   holds a positive diagonal entry.  nnz is the length of col and val.
+ *   The kernel checks the structure before it gathers through it:
+ *   0 <= row_ptr[i] <= row_ptr[i+1] <= nnz and 0 <= col[e] < n, else the
+ *   record's status is GFM_ERR_ARG and nothing else is read or written
+ *   beyond x's start vector.  The GFM system of gfm_assemble is
  *   A_ii = diag_i, A_{own,nb} = A_{nb,own} = -gamma_f (gfm_export_system).
  *   b [n] the right-hand side, x [n] the solution (in: the start vector when
  *   use_x0 = 1).  x may not alias the other arrays.
@@ -278,8 +282,9 @@ gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *
  * timeout_ms bounds each grid-barrier wait as in gfm_solve_opts.  info
  * (nullable) is a DEVICE pointer to one record, written by the kernel
  * (status GFM_OK, GFM_ERR_NOT_CONVERGED, GFM_ERR_BREAKDOWN, GFM_ERR_TIMEOUT,
- * or GFM_ERR_ARG for a row without a positive diagonal).  The call only
- * enqueues work on `stream` and never synchronises.
+ * or GFM_ERR_ARG for a bad CSR structure or a row without a positive
+ * diagonal).  The call only enqueues work on `stream` and never
+ * synchronises.
  *
  * Scratch: the CG vectors, the per-CTA partial sums and the barrier counter
  * live in one fixed array in the library's device code, 8.05 MiB for
@@ -292,13 +297,32 @@ gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *
  * the barrier block is cleared on `stream` at every call, and the rest is
  * written before it is read, but two calls whose work overlaps on the GPU
  * (different streams or host threads) race on it and corrupt each other.
- * Returns GFM_OK once enqueued, GFM_ERR_ARG (n out of range, NULL array,
- * rtol <= 0, max_iters < 0, timeout_ms <= 0), GFM_ERR_CUDA.
+ * Returns GFM_OK once enqueued, GFM_ERR_ARG (n out of range, nnz < n, NULL
+ * array, rtol <= 0, max_iters < 0, timeout_ms <= 0), GFM_ERR_CUDA.
  */
 #define GFM_NOALLOC_MAX_CELLS 262144
-gfm_status gfm_solve_csr_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
-                                 const double *b, double *x, double rtol, int32_t max_iters, int32_t use_x0,
-                                 double timeout_ms, gfm_solve_info *info, gfm_stream stream);
+gfm_status gfm_solve_csr_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col,
+                                 const double *val, const double *b, double *x, double rtol, int32_t max_iters,
+                                 int32_t use_x0, double timeout_ms, gfm_solve_info *info, gfm_stream stream);
+
+/*
+ * Split the tanks of a batch across n_ranks GPUs (one process each).  The
+ * tanks are independent problems (each its own pressure equation of
+ * Sec. 3.1 with its own pin), so the split needs no data exchange: each
+ * rank builds a batched handle of its tanks and only per-tank records are
+ * gathered afterwards.  Balances cells per rank by longest-processing-time
+ * list scheduling (descending cells, ties by tank index; each tank to the
+ * least-loaded rank, ties to the lower rank), so every rank computes the
+ * same table from the same counts.  The busiest rank holds at most
+ * total/n_ranks + (1 - 1/n_ranks) * largest cells.
+ *  cells        : host int64 [n_tanks], cells of each tank (>= 1).
+ *  rank_of_tank : host int32 [n_tanks], out: the rank of each tank.
+ *  rank_cells   : host int64 [n_ranks] or NULL, out: cells per rank.
+ * Host only; needs no GPU.  Errors: GFM_ERR_ARG (NULL, n_tanks or n_ranks
+ * < 1, a tank with no cells).
+ */
+gfm_status gfm_partition_tanks(const int64_t *cells, int32_t n_tanks, int32_t n_ranks, int32_t *rank_of_tank,
+                               int64_t *rank_cells);
 
 /* Launch shape of the persistent kernels (threads a multiple of 32, at most
  * 512).  threads = 0 / ctas_per_sm = 0 keep the current value.  Errors:

@@ -33,6 +33,7 @@ EXPORTED_SYMBOLS = (
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
     "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc", "gfm_autotune",
+    "gfm_partition_tanks",
 )
 
 # largest n accepted by gfm_solve_csr_noalloc (its fixed device scratch)
@@ -131,8 +132,9 @@ def load_library(build_if_missing: bool = True):
         "gfm_get_permutation": ([P, P], S),
         "gfm_set_coarse": ([P, I, I], S),
         "gfm_get_coarse": ([P, ct.POINTER(I), ct.POINTER(I), P, P], S),
-        "gfm_solve_csr_noalloc": ([I, P, P, P, P, P, ct.c_double, I, I, ct.c_double, P, P], S),
+        "gfm_solve_csr_noalloc": ([I, I, P, P, P, P, P, ct.c_double, I, I, ct.c_double, P, P], S),
         "gfm_autotune": ([P, ct.POINTER(_Opts), I, ct.POINTER(_Tuning), ct.POINTER(ct.c_float), P], S),
+        "gfm_partition_tanks": ([P, I, I, P, P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
     }
@@ -474,6 +476,34 @@ class GFMBatch(GFM):
         return [SolveInfo(i.iters, i.refinements, i.status, i.rel_res_l2, i.rel_res_l1) for i in rec]
 
 
+def _check_csr_noalloc(row_ptr, col, val, b, x, info) -> tuple[int, int]:
+    """Host-side checks of solve_csr_noalloc's tensors (no device access):
+    dtypes, sizes (row_ptr [n+1], col and val [nnz], x [n], info at least
+    one record) and one common device.  Returns (n, nnz)."""
+    n = int(b.numel())
+    nnz = int(col.numel())
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col", col, torch.int32), ("val", val, torch.float64),
+                        ("b", b, torch.float64), ("x", x, torch.float64), ("info", info, torch.uint8)):
+        if t.dtype != dt:
+            raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: {name} must be {dt}, got {t.dtype}")
+        if t.device != b.device:
+            raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: {name} is on {t.device}, b on {b.device}")
+    if not 1 <= n <= NOALLOC_MAX_CELLS:
+        raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: n = {n} is outside 1..{NOALLOC_MAX_CELLS}, the "
+                                    "capacity of its fixed device scratch")
+    if row_ptr.numel() != n + 1:
+        raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: row_ptr has {row_ptr.numel()} entries, need n+1 = {n + 1}")
+    if val.numel() != nnz:
+        raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: col has {nnz} entries but val {val.numel()}")
+    if nnz < n or nnz >= 2**31:
+        raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: nnz = {nnz} must be in [n, 2^31)")
+    if x.numel() != n:
+        raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: x has {x.numel()} entries, b {n}")
+    if info.numel() < ct.sizeof(_Info):
+        raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: info needs {ct.sizeof(_Info)} bytes")
+    return n, nnz
+
+
 def solve_csr_noalloc(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, b: torch.Tensor,
                       x: torch.Tensor | None = None, rtol: float = 1e-10, max_iters: int = 1_000_000,
                       use_x0: bool = False, timeout_ms: float = 2000.0, info: torch.Tensor | None = None,
@@ -481,26 +511,23 @@ def solve_csr_noalloc(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tenso
     """FP64 Jacobi-PCG of a CSR system through gfm_solve_csr_noalloc, which
     allocates no device memory (for callers that cannot; its temporaries sit
     in a fixed device array of the library, n <= NOALLOC_MAX_CELLS).  All
-    tensors are caller-owned CUDA tensors (int32 row_ptr/col, FP64 val/b/x);
-    x and info (a 32-byte uint8 device tensor for the result record) are made
-    here when not given.  Returns (x, info tensor); read the record with
-    GFM.info_from_device.  Enqueues only: nothing is synchronised."""
-    lib = load_library()
-    n = int(b.numel())
+    tensors are caller-owned CUDA tensors on one device (int32 row_ptr [n+1]
+    and col [nnz], FP64 val [nnz], b [n] and x [n]); x and info (a uint8
+    device tensor of at least 32 bytes for the result record) are made here
+    when not given.  Sizes, dtypes and devices are checked here; the CSR
+    structure (row bounds, column range) is checked by the kernel, which
+    then reports GFM_ERR_ARG in the record.  Returns (x, info tensor); read
+    the record with GFM.info_from_device.  Enqueues only: nothing is
+    synchronised."""
     if x is None:
-        x = torch.zeros(n, dtype=torch.float64, device=b.device)
+        x = torch.zeros(b.numel(), dtype=torch.float64, device=b.device)
     if info is None:
         info = torch.zeros(ct.sizeof(_Info), dtype=torch.uint8, device=b.device)
-    for t, dt in ((row_ptr, torch.int32), (col, torch.int32), (val, torch.float64), (b, torch.float64),
-                  (x, torch.float64)):
-        if t.dtype != dt:
-            raise GFMError(GFM_ERR_ARG, f"gfm_solve_csr_noalloc: expected {dt}, got {t.dtype}")
-    st = lib.gfm_solve_csr_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x), float(rtol),
+    n, nnz = _check_csr_noalloc(row_ptr, col, val, b, x, info)
+    lib = load_library()
+    st = lib.gfm_solve_csr_noalloc(n, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x), float(rtol),
                                    int(max_iters), int(bool(use_x0)), float(timeout_ms), _ptr(info),
                                    _stream(stream))
     if st != GFM_OK:
-        why = (f"n = {n} is outside 1..{NOALLOC_MAX_CELLS}, the capacity of its fixed device scratch"
-               if st == GFM_ERR_ARG and not 1 <= n <= NOALLOC_MAX_CELLS else
-               lib.gfm_status_string(st).decode())
-        raise GFMError(st, f"gfm_solve_csr_noalloc: {why}")
+        raise GFMError(st, f"gfm_solve_csr_noalloc: {lib.gfm_status_string(st).decode()}")
     return x, info

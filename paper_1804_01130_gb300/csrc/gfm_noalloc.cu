@@ -47,7 +47,7 @@ constexpr size_t kScratchDoubles = kVec + 4 * (size_t)kMaxCells;  // 8.05 MiB at
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 struct Args {
-    int n;
+    int n, nnz;
     const int *rp, *col;
     const double *val, *b;
     double *x;
@@ -180,13 +180,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg_csr_noalloc(Args a)
     const double rtol2 = a.rtol * a.rtol;
     int iters = 0, checks = 0, status = GFM_ERR_NOT_CONVERGED;
 
-    // Jacobi weights from the diagonal entries; a row without a positive one
-    // is an argument error.  Start vector.
+    // Validate the caller's CSR structure before any vector is gathered
+    // through it: 0 <= row_ptr[i] <= row_ptr[i+1] <= nnz and 0 <= col < n.
+    // A row with bad bounds is skipped, so the check itself reads only
+    // row_ptr [n+1] and, within checked bounds, col/val [nnz].  Jacobi
+    // weights from the diagonal entries; a row without a positive one is an
+    // argument error too.  Start vector.  Every row is checked by some CTA
+    // before the barrier, and any error stops every CTA after it.
     int bad = 0;
     for (int i = i0; i < n; i += stride) {
+        const int e0 = a.rp[i], e1 = a.rp[i + 1];
         double d = 0.0;
-        for (int e = a.rp[i]; e < a.rp[i + 1]; ++e)
-            if (a.col[e] == i) d += a.val[e];
+        if (e0 < 0 || e1 < e0 || e1 > a.nnz) {
+            bad = 1;
+        } else {
+            for (int e = e0; e < e1; ++e) {
+                const int c = a.col[e];
+                if (c < 0 || c >= n) bad = 1;
+                else if (c == i) d += a.val[e];
+            }
+        }
         if (!(d > 0.0) || !isfinite(d)) bad = 1;
         dinv[i] = 1.0 / d;
         if (!a.use_x0) a.x[i] = 0.0;
@@ -317,12 +330,13 @@ gfm_status setup_current_device(DeviceScratch &out)
 
 }  // namespace
 
-extern "C" gfm_status gfm_solve_csr_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col,
+extern "C" gfm_status gfm_solve_csr_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col,
                                             const double *val, const double *b, double *x, double rtol,
                                             int32_t max_iters, int32_t use_x0, double timeout_ms,
                                             gfm_solve_info *info, gfm_stream stream)
 {
     if (n < 1 || n > kMaxCells) return GFM_ERR_ARG;  // beyond the fixed scratch capacity
+    if (nnz < n) return GFM_ERR_ARG;                  // every row needs its diagonal entry
     if (!row_ptr || !col || !val || !b || !x) return GFM_ERR_ARG;
     if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iters < 0 || !(timeout_ms > 0.0) || !std::isfinite(timeout_ms))
         return GFM_ERR_ARG;
@@ -334,6 +348,7 @@ extern "C" gfm_status gfm_solve_csr_noalloc(int32_t n, const int32_t *row_ptr, c
     const int want = (n + kThreads - 1) / kThreads;
     Args a;
     a.n = n;
+    a.nnz = nnz;
     a.rp = row_ptr;
     a.col = col;
     a.val = val;

@@ -54,3 +54,30 @@ def test_no_cpu_fallback_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(gfm.GFMError):
         gfm.GFM([0], [1], [[1.0], [0.0], [0.0]], [[0.0, 1.0], [0.0, 0.0], [0.0, 0.0]])
+
+
+def test_noalloc_wrapper_checks_sizes_before_any_device_call():
+    """solve_csr_noalloc rejects inconsistent tensor sizes, dtypes and
+    devices on the host, before it reaches the library (CPU tensors here:
+    each mismatch is caught ahead of the device check)."""
+    import torch
+
+    import paper_1804_01130_gb300 as gfm
+    n, nnz = 10, 28
+
+    def call(rp=n + 1, col=nnz, val=nnz, b=n, x=n, info=32, rp_dtype=torch.int32):
+        return gfm.solve_csr_noalloc(torch.zeros(rp, dtype=rp_dtype), torch.zeros(col, dtype=torch.int32),
+                                     torch.zeros(val, dtype=torch.float64), torch.zeros(b, dtype=torch.float64),
+                                     x=torch.zeros(x, dtype=torch.float64), info=torch.zeros(info, dtype=torch.uint8))
+
+    for bad, match in ((dict(rp=n), "row_ptr"), (dict(val=nnz - 1), "val"), (dict(x=n + 1), "x has"),
+                       (dict(info=16), "info"), (dict(col=n - 1, val=n - 1), "nnz"),
+                       (dict(rp_dtype=torch.int64), "int32"),
+                       (dict(rp=gfm.NOALLOC_MAX_CELLS + 2, b=gfm.NOALLOC_MAX_CELLS + 1,
+                             x=gfm.NOALLOC_MAX_CELLS + 1), "capacity")):
+        with pytest.raises(gfm.GFMError, match=match) as e:
+            call(**bad)
+        assert e.value.status == gfm.GFM_ERR_ARG
+    # consistent sizes get as far as the device check: CPU tensors are refused
+    with pytest.raises(gfm.GFMError, match="CUDA"):
+        call()

@@ -1,6 +1,8 @@
 """gfm_solve_csr_noalloc (the entry point that allocates no device memory)
-against gfm_solve on the same assembled GFM systems, through the C ABI, on
-consecutive calls that share its fixed device scratch."""
+against gfm_solve on the same assembled GFM systems and against the CPU
+oracle's own CSR solve, through the C ABI, on consecutive calls that share
+its fixed device scratch; and its kernel-side checks of the caller's CSR
+structure, which must stop it before it gathers through a bad index."""
 import ctypes as ct
 
 import numpy as np
@@ -8,6 +10,7 @@ import pytest
 import torch
 
 import cases
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -71,7 +74,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     idx = torch.zeros(8, dtype=torch.int32, device="cuda")
     info = torch.zeros(ct.sizeof(g._Info), dtype=torch.uint8, device="cuda")
     p = [ct.c_void_p(t.data_ptr()) for t in (idx, idx, small, small, small)]
-    st = lib.gfm_solve_csr_noalloc(g.NOALLOC_MAX_CELLS + 1, *p, 1e-10, 100, 0, 1000.0,
+    st = lib.gfm_solve_csr_noalloc(g.NOALLOC_MAX_CELLS + 1, g.NOALLOC_MAX_CELLS + 1, *p, 1e-10, 100, 0, 1000.0,
                                    ct.c_void_p(info.data_ptr()), None)
     assert st == g.GFM_ERR_ARG
     with pytest.raises(g.GFMError, match="capacity"):
@@ -96,3 +99,79 @@ def test_noalloc_reports_a_missing_diagonal():
            torch.tensor(vals, dtype=torch.float64, device=dev), torch.ones(n, dtype=torch.float64, device=dev))
     _, info = _solve(csr)
     assert info.status == _g().GFM_ERR_ARG
+
+
+def _oracle_csr(c):
+    """The oracle's assembled CSR system (CPU, FP64) on the device, and the
+    oracle's own solution of it."""
+    sy = oracle.assemble(c, oracle.faces(c))
+    x_ref, _, rel, st = oracle.pcg(sy, rtol=1e-13)
+    assert st == 0
+    dev = torch.device("cuda")
+    csr = (torch.as_tensor(sy.rowptr.astype(np.int32), device=dev), torch.as_tensor(sy.col, device=dev),
+           torch.as_tensor(sy.val, device=dev), torch.as_tensor(sy.b, device=dev))
+    return csr, x_ref
+
+
+def test_noalloc_matches_the_oracle_csr_solve():
+    """On the oracle's own matrix (not the library's assembly), two calls in
+    a row, the second on a larger system than the first."""
+    for c in (cases.make_case(1), cases.box_case(20, 16, 6, seed=9, permute=True, alpha_noise=0.05)):
+        csr, x_ref = _oracle_csr(c)
+        x, info = _solve(csr, rtol=1e-13)
+        assert info.status == 0, info
+        err = np.linalg.norm(x.cpu().numpy() - x_ref) / np.linalg.norm(x_ref)
+        assert err <= 1e-9, (c.n, err)
+
+
+def _laplace_1d(n):
+    rp, cols, vals = [0], [], []
+    for i in range(n):
+        for j, v in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                cols.append(j)
+                vals.append(v)
+        rp.append(len(cols))
+    return rp, cols, vals
+
+
+def _call_raw(rp, cols, vals, n, nnz=None):
+    """Straight through the C ABI with the given structure; returns the record."""
+    g = _g()
+    lib = g.load_library()
+    dev = torch.device("cuda")
+    trp = torch.tensor(rp, dtype=torch.int32, device=dev)
+    tcol = torch.tensor(cols, dtype=torch.int32, device=dev)
+    tval = torch.tensor(vals, dtype=torch.float64, device=dev)
+    b = torch.ones(n, dtype=torch.float64, device=dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    info = torch.zeros(ct.sizeof(g._Info), dtype=torch.uint8, device=dev)
+    nnz = len(cols) if nnz is None else nnz
+    st = lib.gfm_solve_csr_noalloc(n, nnz, *[ct.c_void_p(t.data_ptr()) for t in (trp, tcol, tval, b, x)], 1e-10,
+                                   1000, 0, 1000.0, ct.c_void_p(info.data_ptr()), None)
+    assert st == g.GFM_OK
+    torch.cuda.synchronize()
+    return g.GFM.info_from_device(info)
+
+
+def test_noalloc_rejects_a_column_out_of_range():
+    n = 64
+    rp, cols, vals = _laplace_1d(n)
+    cols[3 * 20 + 1] = n + 5  # a slot of row 20 points past the last row
+    assert _call_raw(rp, cols, vals, n).status == _g().GFM_ERR_ARG
+    rp, cols, vals = _laplace_1d(n)
+    cols[7] = -1
+    assert _call_raw(rp, cols, vals, n).status == _g().GFM_ERR_ARG
+
+
+def test_noalloc_rejects_bad_row_bounds():
+    n = 64
+    rp, cols, vals = _laplace_1d(n)
+    bad = list(rp)
+    bad[10], bad[11] = bad[11], bad[10]  # row 10 ends before it starts
+    assert _call_raw(bad, cols, vals, n).status == _g().GFM_ERR_ARG
+    # the last row reaches past nnz (the arrays are large enough: nnz is the
+    # length the caller declares)
+    assert _call_raw(rp, cols, vals, n, nnz=len(cols) - 2).status == _g().GFM_ERR_ARG
+    # the same structure, well formed, still solves afterwards
+    assert _call_raw(rp, cols, vals, n).status == _g().GFM_OK
