@@ -28,6 +28,8 @@ __all__ = [
     "random_face_flux",
     "stokes2_eta",
     "make_case",
+    "batch_shapes",
+    "batch_cases",
     "column_case",
     "still_water_case",
     "box_case",
@@ -412,8 +414,9 @@ def green_water_box(nx: int, ny: int, nz: int, seed: int, permute: bool = True) 
                       meta=dict(seed=seed, permuted=permute))
 
 
-def batch_cases(ntanks: int = 64, seed0: int = 4000, nx_range=(128, 1024), ny_range=(64, 256)) -> list:
-    """Batch of 2D wave tanks of uneven size (tank t uses seed seed0 + t)."""
+def batch_shapes(ntanks: int = 64, seed0: int = 4000, nx_range=(128, 1024), ny_range=(64, 256)) -> list:
+    """(nx, ny, ka, wavelengths) of each tank of a batch (tank t uses seed
+    seed0 + t), without building the tanks."""
     out = []
     for t in range(ntanks):
         rng = np.random.default_rng(seed0 + t)
@@ -421,6 +424,18 @@ def batch_cases(ntanks: int = 64, seed0: int = 4000, nx_range=(128, 1024), ny_ra
         ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
         ka = float(rng.uniform(0.02, 0.15))
         nw = int(rng.integers(1, 7))
+        out.append((nx, ny, ka, nw))
+    return out
+
+
+def batch_cases(ntanks: int = 64, seed0: int = 4000, nx_range=(128, 1024), ny_range=(64, 256),
+                only=None) -> list:
+    """Batch of 2D wave tanks of uneven size (tank t uses seed seed0 + t).
+    ``only`` (optional): the tank indices to build, in the order given."""
+    shapes = batch_shapes(ntanks, seed0, nx_range, ny_range)
+    out = []
+    for t in (range(ntanks) if only is None else only):
+        nx, ny, ka, nw = shapes[t]
         out.append(_wave_tank(nx, ny, 16.0, 4.0, 2.0, ka, nw, seed0 + 10_000 + t, f"tank{t}_{nx}x{ny}",
                               1e-8, "mixed"))
     return out

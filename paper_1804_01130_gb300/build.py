@@ -28,6 +28,7 @@ UNITS = {
     "gfm_coarse.cu": [],
     "gfm_setup.cpp": [],
     "gfm_noalloc.cu": ["-Xptxas", "-v"],
+    "gfm_shard.cpp": [],
 }
 HEADERS = ["gfm_internal.h", "gfm_setup.h"]
 
