@@ -4,10 +4,10 @@ times (default launch shape, the workloads' renumbering and tolerances):
 - the 1024x512 wave tank (524 288 cells): full arrays against the oracle;
 - the 256x128x128 green-water box (4.2M cells, permuted), whose tables are
   streamed through shared-memory stages: full assembly, the true residual
-  of the solution through the oracle's own matrix, and the solution against
-  the oracle's CG;
+  of the solution through the oracle's own matrix, and the FP64 and mixed
+  solutions against the oracle's CG;
 - the 64-tank batch (5.2M cells in one launch): per-tank assembly and true
-  residuals, and sampled tanks against the oracle's solution.
+  residuals, and every tank against the oracle's solution.
 
 Bars as in the small-case tests: assembly bit-exact, p_d within relative L2
 1e-9 (FP64) / 1e-6 (mixed) of the oracle, true residuals at the requested
@@ -82,15 +82,15 @@ def test_box3d_256x128x128_full_size():
     p, _, info = s.solve(mode="mixed", rtol=1e-8)
     assert info.status == 0
     assert _true_rel(sy, p.cpu().numpy()) <= 1.05e-8
-    # against the oracle's solution
-    p_ref, it, rel, st = oracle.pcg(sy, rtol=1e-11)
-    assert st == 0
+    # against the oracle's solution: FP64 at the 1e-9 bar, mixed at 1e-6
+    p_ref, it, rel, st = oracle.pcg(sy, rtol=1e-13)
+    assert st == 0 and rel <= 1e-13
     pm, _, im = s.solve(mode="mixed", rtol=1e-10)
     assert im.status == 0
     assert _rel(pm.cpu().numpy(), p_ref) <= 1e-6
-    p64, _, i64 = s.solve(mode="fp64", rtol=1e-10)
+    p64, _, i64 = s.solve(mode="fp64", rtol=1e-12)
     assert i64.status == 0
-    assert _rel(p64.cpu().numpy(), pm.cpu().numpy()) <= 1e-6
+    assert _rel(p64.cpu().numpy(), p_ref) <= 1e-9
 
 
 def test_batch64_full_size():
@@ -124,12 +124,12 @@ def test_batch64_full_size():
         systems.append((c0, sy))
         c0 += t.n
         f0 += t.F
-    # sampled tanks against the oracle's solution
+    # every tank against the oracle's solution
     p2, _, infos2 = b.solve(rtol=1e-10)
     p2n = p2.cpu().numpy()
-    rng = np.random.default_rng(4064)
-    for k in rng.choice(len(tanks), 4, replace=False):
-        c0, sy = systems[k]
+    worst = 0.0
+    for k, (c0, sy) in enumerate(systems):
         p_ref, _, _, st = oracle.pcg(sy, rtol=1e-11)
-        assert st == 0 and infos2[k].status == 0
-        assert _rel(p2n[c0:c0 + tanks[k].n], p_ref) <= 1e-6
+        assert st == 0 and infos2[k].status == 0, (k, infos2[k])
+        worst = max(worst, _rel(p2n[c0:c0 + tanks[k].n], p_ref))
+    assert worst <= 1e-6, worst
