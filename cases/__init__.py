@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "Case",
     "structured_mesh",
+    "graded_mesh",
     "permute_mesh",
     "alpha_cut_2d",
     "alpha_subsampled_3d",
@@ -122,6 +123,59 @@ def structured_mesh(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float,
         owner=owner[order].astype(np.int32), neighbour=neighbour[order].astype(np.int32),
         Sf=np.ascontiguousarray(Sf[:, order]), C=C, V=V, xf=np.ascontiguousarray(xfc[:, order]),
         dims=(nx, ny, nz), spacing=(dx, dy, dz), origin=tuple(origin),
+    )
+
+
+def graded_mesh(xn, yn, zn) -> dict:
+    """Tensor-product hex mesh from node coordinates (cells of uneven size),
+    in the same face-addressed form and cell numbering as structured_mesh.
+    Face centres lie on the line between the two cell centres, but not
+    half-way between them."""
+    xn, yn, zn = (np.asarray(v, dtype=np.float64) for v in (xn, yn, zn))
+    nx, ny, nz = xn.size - 1, yn.size - 1, zn.size - 1
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % nx
+    j = (idx // nx) % ny
+    k = idx // (nx * ny)
+    dxs, dys, dzs = np.diff(xn), np.diff(yn), np.diff(zn)
+    C = np.empty((3, n))
+    C[0] = 0.5 * (xn[i] + xn[i + 1])
+    C[1] = 0.5 * (yn[j] + yn[j + 1])
+    C[2] = 0.5 * (zn[k] + zn[k + 1])
+    V = dxs[i] * dys[j] * dzs[k]
+    own, nb, S, XF = [], [], [], []
+    for axis, step, ok in ((0, 1, i < nx - 1), (1, nx, j < ny - 1), (2, nx * ny, k < nz - 1)):
+        o = idx[ok]
+        if o.size == 0:
+            continue
+        io, jo, ko = i[ok], j[ok], k[ok]
+        s = np.zeros((3, o.size))
+        xf = C[:, o].copy()
+        if axis == 0:
+            s[0] = dys[jo] * dzs[ko]
+            xf[0] = xn[io + 1]
+        elif axis == 1:
+            s[1] = dxs[io] * dzs[ko]
+            xf[1] = yn[jo + 1]
+        else:
+            s[2] = dxs[io] * dys[jo]
+            xf[2] = zn[ko + 1]
+        own.append(o)
+        nb.append(o + step)
+        S.append(s)
+        XF.append(xf)
+    owner = np.concatenate(own)
+    neighbour = np.concatenate(nb)
+    Sf = np.concatenate(S, axis=1)
+    xfc = np.concatenate(XF, axis=1)
+    order = np.lexsort((neighbour, owner))
+    return dict(
+        n=n, F=owner.size,
+        owner=owner[order].astype(np.int32), neighbour=neighbour[order].astype(np.int32),
+        Sf=np.ascontiguousarray(Sf[:, order]), C=C, V=V, xf=np.ascontiguousarray(xfc[:, order]),
+        dims=(nx, ny, nz), spacing=(float(dxs.min()), float(dys.min()), float(dzs.min())),
+        origin=(float(xn[0]), float(yn[0]), float(zn[0])),
     )
 
 

@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
 _lib = None
 
 (MUT_NONE, MUT_JUMP_SIGN_EQ15, MUT_LAMBDA_FROM_OWNER, MUT_ARITH_BETA, MUT_DROP_JUMP, MUT_SWAP_ALPHA_DERIV,
- MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ) = range(8)
+ MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ, MUT_GHOST_SWAP_BETA) = range(9)
 KIND_DRY, KIND_WET, KIND_IF_OWNER_WET, KIND_IF_OWNER_DRY = range(4)
 
 
@@ -63,6 +63,10 @@ def _load():
         lib.gfm_oracle_ghost_route.restype = None
         lib.gfm_oracle_adjoint_chain.argtypes = [I, I, P, P, P, P, P, P, P, P, D, D, P, P, P, P, P, P, I]
         lib.gfm_oracle_adjoint_chain.restype = None
+        lib.gfm_oracle_gradient.argtypes = [I, I, P, P, P, P, P, P, P, D, D, P, P, P, I]
+        lib.gfm_oracle_gradient.restype = None
+        lib.gfm_oracle_reconstruct.argtypes = [I, I, P, P, P, P, P, P, P]
+        lib.gfm_oracle_reconstruct.restype = None
         lib.gfm_oracle_set_threads.argtypes = [I]
         lib.gfm_oracle_set_threads.restype = None
         lib.gfm_oracle_max_threads.restype = I
@@ -224,6 +228,34 @@ def adjoint_chain(case, fc: Faces, p: np.ndarray, mu: np.ndarray, alpha=None, mu
                                      _p(_f64(case.g)), _p(_f64(p)), _p(_f64(mu)), _p(dphi), _p(dalpha), _p(dlam),
                                      int(mutate))
     return dphi, dalpha, dlam
+
+
+def gradient(case, p: np.ndarray, alpha=None, xf=None, use_xf: bool = True, mutate: int = MUT_NONE) -> np.ndarray:
+    """(1/rho) grad p_d per cell [3, n]: Gauss theorem with the Eq. 20 ghost
+    values at interface faces (see gfm_oracle.c).  Face centres: ``xf``, else
+    the case's own (case.xf) when use_xf, else midpoints of the centres."""
+    n, F = case.n, case.F
+    alpha = _f64(case.alpha if alpha is None else alpha)
+    if xf is None and use_xf:
+        xf = case.xf
+    xfp = _p(_f64(xf)) if xf is not None else None
+    out = np.empty((3, n))
+    _load().gfm_oracle_gradient(n, F, _p(_i32(case.owner)), _p(_i32(case.neighbour)), _p(_f64(case.Sf)),
+                                _p(_f64(case.C)), _p(_f64(case.V)), xfp, _p(alpha), case.rho_w, case.rho_a,
+                                _p(_f64(case.g)), _p(_f64(p)), _p(out), int(mutate))
+    return out
+
+
+def reconstruct(case, phi: np.ndarray, xf=None, use_xf: bool = True) -> np.ndarray:
+    """Cell velocity [3, n] from face fluxes: U_P = sum_f phi_Pf (x_f - x_P) / V_P."""
+    n, F = case.n, case.F
+    if xf is None and use_xf:
+        xf = case.xf
+    xfp = _p(_f64(xf)) if xf is not None else None
+    out = np.empty((3, n))
+    _load().gfm_oracle_reconstruct(n, F, _p(_i32(case.owner)), _p(_i32(case.neighbour)), _p(_f64(case.C)),
+                                   _p(_f64(case.V)), xfp, _p(_f64(phi)), _p(out))
+    return out
 
 
 def solve(case, rtol: float | None = None, direct: bool | None = None, alpha=None, phi=None, mutate: int = MUT_NONE,

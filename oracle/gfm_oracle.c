@@ -56,6 +56,7 @@
 #define MUT_SWAP_ALPHA_DERIV 5  /* swap d lambda/d alpha_W and d alpha_D        */
 #define MUT_PCG_NO_PRECOND 6    /* fixed-count PCG: drop the Jacobi weights      */
 #define MUT_PCG_STALE_RZ 7      /* fixed-count PCG: never update r.z             */
+#define MUT_GHOST_SWAP_BETA 8   /* gradient: wet-side ghost weighted by beta+    */
 
 int gfm_oracle_version(void) { return 3; }
 
@@ -503,4 +504,106 @@ void gfm_oracle_adjoint_chain(int n, int F, const int32_t *owner, const int32_t 
         }
         if (dL_dlambda) dL_dlambda[f] = dlam;
     }
+}
+
+/*
+ * Dynamic-pressure gradient of the momentum equation with the ghost values
+ * of Sec. 3.1 (Eq. 2's pressure term (1/rho) grad p_d, Gauss theorem,
+ * cell-centre-to-face interpolation corrected at the interface).
+ * For each internal face f between cells o and nb, each side P sees the
+ * other cell N through a face value
+ *   pf(P) = w_P p_P + (1 - w_P) pN~,   w_P = S.(x_N - x_f) / S.(x_N - x_P)
+ * (linear interpolation weight from the face centre x_f; the midpoint of the
+ * two cell centres when xf is NULL), where pN~ = p_N off the interface and,
+ * on an interface face (W wet, D dry, lambda from the wet cell, Eq. 13;
+ * x_Gamma by Eq. 12; H = p_d- - p_d+ = (rho_w - rho_a) g.x_Gamma, Eq. 7;
+ * beta+ = 1/rho_w, beta- = 1/rho_a, Eq. 14; beta_w by Eq. 18):
+ *   seen from W:  pD~ = (beta-/beta_w) p_D + (1 - beta-/beta_w) p_W - (beta-/beta_w) H     (Eq. 20)
+ *   seen from D:  pW~ = (beta+/beta_w) p_W + (1 - beta+/beta_w) p_D + (beta+/beta_w) H     (the
+ *                 analogous extrapolation into the light fluid: the same jump
+ *                 conditions, Eqs. 15-16, solved for p_d- and carried on to W)
+ * Walls carry zero-gradient p_d, so their face value is p_P and, the cell
+ * being closed, the Gauss sum reduces to the internal faces in difference
+ * form:
+ *   grad_P = beta_P / V_P * sum_f (pf(P) - p_P) S_Pf,   S_Pf = +S_f (P owner), -S_f (P neighbour),
+ * with beta_P = 1/rho of P's own phase (wet: alpha >= 0.5).  Per-cell sums
+ * run in ascending face order.  grad is [3][n].  `mutate` plants a mistake
+ * for the tests (0 = faithful).
+ */
+void gfm_oracle_gradient(int n, int F, const int32_t *owner, const int32_t *neighbour,
+                         const double *Sf, const double *C, const double *V, const double *xf,
+                         const double *alpha, double rho_w, double rho_a, const double *g,
+                         const double *p, double *grad, int mutate)
+{
+    const double bp = 1.0 / rho_w, bm = 1.0 / rho_a;
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) grad[k] = 0.0;
+    for (int f = 0; f < F; ++f) {
+        int o = owner[f], nb = neighbour[f];
+        double S[3], x[3];
+        for (int k = 0; k < 3; ++k) {
+            S[k] = Sf[(size_t)k * F + f];
+            x[k] = xf ? xf[(size_t)k * F + f] : 0.5 * (C[(size_t)k * n + o] + C[(size_t)k * n + nb]);
+        }
+        /* weights: w_o = S.(x_nb - x_f)/S.d, w_nb = S.(x_f - x_o)/S.d */
+        double sd = 0.0, snf = 0.0, sfo = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double xo = C[(size_t)k * n + o], xn = C[(size_t)k * n + nb];
+            sd += S[k] * (xn - xo);
+            snf += S[k] * (xn - x[k]);
+            sfo += S[k] * (x[k] - xo);
+        }
+        double w_o = snf / sd, w_nb = sfo / sd;
+        int wo = alpha[o] >= 0.5, wn = alpha[nb] >= 0.5;
+        double ghost_for_o = p[nb], ghost_for_nb = p[o];
+        if (wo != wn) {
+            int W = wo ? o : nb, D = wo ? nb : o;
+            double lam = (alpha[W] - 0.5) / (alpha[W] - alpha[D]);
+            double xg[3];
+            for (int k = 0; k < 3; ++k)
+                xg[k] = C[(size_t)k * n + W] + lam * (C[(size_t)k * n + D] - C[(size_t)k * n + W]);
+            double H = -(rho_a - rho_w) * (g[0] * xg[0] + g[1] * xg[1] + g[2] * xg[2]);
+            if (mutate == MUT_JUMP_SIGN_EQ15) H = -H;
+            if (mutate == MUT_DROP_JUMP) H = 0.0;
+            double bw = lam * bm + (1.0 - lam) * bp;
+            double rW = (mutate == MUT_GHOST_SWAP_BETA) ? bp / bw : bm / bw;
+            double gD = rW * p[D] + (1.0 - rW) * p[W] - rW * H; /* D's value seen from W */
+            double gW = (bp / bw) * p[W] + (1.0 - bp / bw) * p[D] + (bp / bw) * H; /* W's value seen from D */
+            if (W == o) { ghost_for_o = gD; ghost_for_nb = gW; }
+            else { ghost_for_o = gW; ghost_for_nb = gD; }
+        }
+        double pf_o = w_o * p[o] + (1.0 - w_o) * ghost_for_o;
+        double pf_nb = w_nb * p[nb] + (1.0 - w_nb) * ghost_for_nb;
+        for (int k = 0; k < 3; ++k) {
+            grad[(size_t)k * n + o] += (pf_o - p[o]) * S[k];
+            grad[(size_t)k * n + nb] -= (pf_nb - p[nb]) * S[k];
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double be = (alpha[i] >= 0.5) ? bp : bm;
+        for (int k = 0; k < 3; ++k) grad[(size_t)k * n + i] = be * grad[(size_t)k * n + i] / V[i];
+    }
+}
+
+/*
+ * Cell velocity from face fluxes (the flux/velocity reconstruction that
+ * follows the pressure solve): for a closed cell, sum_f (u.S_f)(x_f - x_P)
+ * = V_P u for any uniform u, so
+ *   U_P = 1/V_P * sum_f phi_Pf (x_f - x_P),   phi_Pf = +phi_f (P owner), -phi_f (P neighbour),
+ * over internal faces; wall faces carry no flux.  Face centres as in
+ * gfm_oracle_gradient (midpoints when xf is NULL).  U is [3][n].
+ */
+void gfm_oracle_reconstruct(int n, int F, const int32_t *owner, const int32_t *neighbour,
+                            const double *C, const double *V, const double *xf, const double *phi, double *U)
+{
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) U[k] = 0.0;
+    for (int f = 0; f < F; ++f) {
+        int o = owner[f], nb = neighbour[f];
+        for (int k = 0; k < 3; ++k) {
+            double x = xf ? xf[(size_t)k * F + f] : 0.5 * (C[(size_t)k * n + o] + C[(size_t)k * n + nb]);
+            U[(size_t)k * n + o] += phi[f] * (x - C[(size_t)k * n + o]);
+            U[(size_t)k * n + nb] -= phi[f] * (x - C[(size_t)k * n + nb]);
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) U[(size_t)k * n + i] /= V[i];
 }
