@@ -257,6 +257,32 @@ gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *
                           const gfm_solve_opts *opts, double *p_host, gfm_solve_info *info, gfm_stream stream);
 
 /*
+ * Dynamic-pressure gradient of the momentum equation and cell velocities
+ * (Sec. 3.1: Eq. 20 and the paragraph after it, which carries the ghost
+ * values into the pressure gradient of Eq. 2; Eq. 8).  After gfm_assemble,
+ * for a p_d [n] (e.g. gfm_solve's), caller order throughout:
+ *   grad [3][n] (nullable): (1/rho grad p_d)_P by the Gauss theorem, linear
+ *        cell-to-face interpolation, the neighbour's value replaced at an
+ *        interface face by its ghost value in P's fluid (Eq. 20 from the wet
+ *        side, the analogous extrapolation from the dry side); zero-gradient
+ *        walls.  The ghost values collapse onto the assembled coefficients:
+ *          grad_P = 1/V_P sum_f (1 - w_P) (p_N - p_P - s_Pf J_f)/rho_f s_Pf S_f,
+ *        rho_f = lambda_f rho_w + (1 - lambda_f) rho_a, s_Pf = +1 (P owns f) or -1,
+ *        1 - w_P = S_f.(x_f - x_P)/S_f.(x_N - x_P).  Zero in still water.
+ *   U [3][n] (nullable; needs phi [F]): cell velocity from the face flux phi
+ *        (e.g. gfm_solve's corrected flux), U_P = 1/V_P sum_f s_Pf phi_f (x_f - x_P),
+ *        exact for a uniform velocity.
+ *   V  [n]     cell volumes (required).
+ *   xf [3][F]  face centres, or NULL for the midpoints of the two cell centres
+ *              (exact on uniform hex meshes).
+ * Works on batched handles (densities per tank).  One kernel launch, FP64.
+ * Errors: GFM_ERR_ARG (NULL p or V, both outputs NULL, U without phi),
+ * GFM_ERR_STATE (grad before gfm_assemble), GFM_ERR_CUDA.
+ */
+gfm_status gfm_gradient(gfm_handle h, const double *p, const double *V, const double *xf, double *grad,
+                        const double *phi, double *U, gfm_stream stream);
+
+/*
  * Solve without device allocation.  The paper has no counterpart: this is an
  * entry point for callers that cannot call cudaMalloc -- code running inside
  * a host program that owns the GPU's memory (a CFD code or plugin drawing

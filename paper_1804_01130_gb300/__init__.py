@@ -33,7 +33,7 @@ EXPORTED_SYMBOLS = (
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
     "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc", "gfm_autotune",
-    "gfm_partition_tanks",
+    "gfm_partition_tanks", "gfm_gradient",
 )
 
 # largest n accepted by gfm_solve_csr_noalloc (its fixed device scratch)
@@ -135,6 +135,7 @@ def load_library(build_if_missing: bool = True):
         "gfm_solve_csr_noalloc": ([I, I, P, P, P, P, P, ct.c_double, I, I, ct.c_double, P, P], S),
         "gfm_autotune": ([P, ct.POINTER(_Opts), I, ct.POINTER(_Tuning), ct.POINTER(ct.c_float), P], S),
         "gfm_partition_tanks": ([P, I, I, P, P], S),
+        "gfm_gradient": ([P, P, P, P, P, P, P, P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
     }
@@ -312,6 +313,22 @@ class GFM:
                                      ct.byref(info), _stream(stream))
         self._check(st, "gfm_solve_host")
         return SolveInfo(info.iters, info.refinements, info.status, info.rel_res_l2, info.rel_res_l1)
+
+    def gradient(self, p: torch.Tensor, V, xf=None, phi: torch.Tensor | None = None, want_grad: bool = True,
+                 stream=None):
+        """(1/rho) grad p_d [3, n] with the GFM ghost values (None unless
+        want_grad) and, when phi [F] is given, the cell velocity [3, n]
+        reconstructed from it (gfm_gradient)."""
+        d = self.device
+        p = _f64(p, d)
+        V = _f64(V, d)
+        xf = None if xf is None else _f64(xf, d).reshape(3, -1).contiguous()
+        phi = None if phi is None else _f64(phi, d)
+        grad = torch.empty((3, self.n), dtype=torch.float64, device=d) if want_grad else None
+        U = torch.empty((3, self.n), dtype=torch.float64, device=d) if phi is not None else None
+        self._check(self.lib.gfm_gradient(self.h, _ptr(p), _ptr(V), _ptr(xf), _ptr(grad), _ptr(phi), _ptr(U),
+                                          _stream(stream)), "gfm_gradient")
+        return grad, U
 
     def set_tuning(self, threads=0, ctas_per_sm=0):
         self._check(self.lib.gfm_set_tuning(self.h, ct.byref(_Tuning(int(threads), int(ctas_per_sm)))),

@@ -29,6 +29,7 @@ UNITS = {
     "gfm_setup.cpp": [],
     "gfm_noalloc.cu": ["-Xptxas", "-v"],
     "gfm_shard.cpp": [],
+    "gfm_gradient.cu": [],
 }
 HEADERS = ["gfm_internal.h", "gfm_setup.h"]
 

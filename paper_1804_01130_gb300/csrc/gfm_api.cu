@@ -974,6 +974,43 @@ gfm_status gfm_solve_host(gfm_handle h, const double *alpha_host, const double *
     return finish_info(h, opts, info, s);
 }
 
+gfm_status gfm_gradient(gfm_handle h, const double *p, const double *V, const double *xf, double *grad,
+                        const double *phi, double *U, gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    if (!p || !V) return fail(h, GFM_ERR_ARG, "p and V must be non-NULL");
+    if (!grad && !U) return fail(h, GFM_ERR_ARG, "nothing to compute: grad and U are both NULL");
+    if (U && !phi) return fail(h, GFM_ERR_ARG, "U needs the face flux phi");
+    if (grad && !h->assembled) return fail(h, GFM_ERR_STATE, "gradient before assemble");
+    clear_stale_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    gfm::GradArgs a{};
+    a.m = sell_of(h);
+    a.n = h->n;
+    a.F = h->F;
+    a.iperm = h->iperm;
+    a.owner = h->owner;
+    a.neighbour = h->neighbour;
+    a.Sf = h->Sf;
+    a.C = h->C;
+    a.V = V;
+    a.xf = xf;
+    a.lambda = h->lambda;
+    a.jump = h->jump;
+    a.p = p;
+    a.phi = phi;
+    a.rho_w = h->phys.rho_w;
+    a.rho_a = h->phys.rho_a;
+    a.stank = h->batched ? h->stank : nullptr;
+    a.tphys = h->batched ? h->tphys : nullptr;
+    a.grad = grad;
+    a.U = U;
+    GFM_CUDA(h, gfm::launch_gradient(a, s));
+    h->prof.launches = 1;
+    h->prof.launches_total += 1;
+    return GFM_OK;
+}
+
 gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t)
 {
     if (!h || !t) return GFM_ERR_ARG;

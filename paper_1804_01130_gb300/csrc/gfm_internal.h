@@ -200,6 +200,23 @@ struct AdjointArgs {
 cudaError_t launch_adjoint_faces(const AdjointArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint_cells(const AdjointArgs &a, cudaStream_t s);
 
+// ---- gradient and velocity reconstruction (gfm_gradient.cu) ----------------
+struct GradArgs {
+    Sell m;
+    int32_t n, F;
+    const int32_t *iperm;              // internal -> caller (-1 padding)
+    const int32_t *owner, *neighbour;  // caller order
+    const double *Sf, *C, *V, *xf;     // xf nullable: face centres half-way between cell centres
+    const double *lambda, *jump;       // assembled interface fraction and oriented jump
+    const double *p;                   // caller order p_d
+    const double *phi;                 // face flux for U (nullable when U is)
+    double rho_w, rho_a;
+    const int32_t *stank;              // batched: tank of each slice (else nullptr)
+    const TankPhys *tphys;             // batched: densities per tank
+    double *grad, *U;                  // [3][n] caller order, either nullable
+};
+cudaError_t launch_gradient(const GradArgs &a, cudaStream_t s);
+
 cudaError_t launch_gather(const double *src_user, const int32_t *iperm, double *dst_internal, int32_t n,
                           int32_t n_pad, cudaStream_t s);
 

@@ -1,11 +1,12 @@
 """GPU parity at the benchmark sizes, in the launch configuration bench.py
 times (default launch shape, the workloads' renumbering and tolerances):
 
-- the 1024x512 wave tank (524 288 cells): full arrays against the oracle;
+- the 1024x512 wave tank (524 288 cells): full arrays against the oracle,
+  and the GFM pressure gradient and velocity reconstruction;
 - the 256x128x128 green-water box (4.2M cells, permuted), whose tables are
   streamed through shared-memory stages: full assembly, the true residual
-  of the solution through the oracle's own matrix, and the FP64 and mixed
-  solutions against the oracle's CG;
+  of the solution through the oracle's own matrix, the FP64 and mixed
+  solutions against the oracle's CG, and the gradient and reconstruction;
 - the 64-tank batch (5.2M cells in one launch): per-tank assembly and true
   residuals, and every tank against the oracle's solution.
 
@@ -58,12 +59,30 @@ def _assembly_bit_exact(s, c):
     return sy
 
 
+def _gradient_matches(s, c, p_ref):
+    """gfm_gradient at full size on the oracle's p_d against the oracle's
+    Eq. 20 ghost-value gradient, and the velocity reconstructed from the
+    oracle's corrected flux (bars as in test_gpu_gradient)."""
+    fc = oracle.faces(c)
+    phi_corr = oracle.corrected_flux(c, fc, p_ref)
+    G, U = s.gradient(torch.as_tensor(p_ref), torch.as_tensor(c.V), xf=torch.as_tensor(c.xf),
+                      phi=torch.as_tensor(phi_corr))
+    G_ref = oracle.gradient(c, p_ref)
+    U_ref = oracle.reconstruct(c, phi_corr)
+    sv = np.max(np.linalg.norm(c.Sf, axis=0)) / np.min(c.V)
+    tol = 1e-12 * np.max(np.abs(p_ref)) * sv / c.rho_a + 1e-12 * np.max(np.abs(G_ref))
+    assert np.max(np.abs(G.cpu().numpy() - G_ref)) <= tol
+    utol = 1e-12 * np.max(np.abs(phi_corr)) * sv + 1e-12 * np.max(np.abs(U_ref))
+    assert np.max(np.abs(U.cpu().numpy() - U_ref)) <= utol
+
+
 def test_tank2d_1024x512_full_size():
     c = cases.make_case(2)
     s = _assembled(c, renumber=1)
     sy = _assembly_bit_exact(s, c)
     p_ref, it, rel, st = oracle.pcg(sy, rtol=1e-13)
     assert st == 0 and rel <= 1e-13
+    _gradient_matches(s, c, p_ref)
     p64, _, i64 = s.solve(mode="fp64", rtol=1e-12)
     assert i64.status == 0
     assert _rel(p64.cpu().numpy(), p_ref) <= 1e-9
@@ -85,6 +104,7 @@ def test_box3d_256x128x128_full_size():
     # against the oracle's solution: FP64 at the 1e-9 bar, mixed at 1e-6
     p_ref, it, rel, st = oracle.pcg(sy, rtol=1e-13)
     assert st == 0 and rel <= 1e-13
+    _gradient_matches(s, c, p_ref)
     pm, _, im = s.solve(mode="mixed", rtol=1e-10)
     assert im.status == 0
     assert _rel(pm.cpu().numpy(), p_ref) <= 1e-6
