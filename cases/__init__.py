@@ -23,6 +23,8 @@ __all__ = [
     "Case",
     "structured_mesh",
     "graded_mesh",
+    "quad_mesh",
+    "wavy_mesh",
     "permute_mesh",
     "alpha_cut_2d",
     "alpha_subsampled_3d",
@@ -177,6 +179,73 @@ def graded_mesh(xn, yn, zn) -> dict:
         dims=(nx, ny, nz), spacing=(float(dxs.min()), float(dys.min()), float(dzs.min())),
         origin=(float(xn[0]), float(yn[0]), float(zn[0])),
     )
+
+
+def quad_mesh(X, Y, dz: float) -> dict:
+    """2D mesh of convex quadrilaterals from node coordinates X, Y of shape
+    (ny + 1, nx + 1), extruded one cell deep (dz), in the face-addressed form
+    and cell numbering of structured_mesh.  Cell centres are polygon
+    centroids, face centres edge midpoints, area vectors the edge normals
+    times dz pointing to the higher-numbered cell.  Cells need not be
+    orthogonal: d_f and S_f are generally not parallel."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    ny, nx = X.shape[0] - 1, X.shape[1] - 1
+    n = nx * ny
+    # vertices counter-clockwise: (i,j), (i+1,j), (i+1,j+1), (i,j+1)
+    vx = np.stack([X[:-1, :-1], X[:-1, 1:], X[1:, 1:], X[1:, :-1]], axis=-1).reshape(n, 4)
+    vy = np.stack([Y[:-1, :-1], Y[:-1, 1:], Y[1:, 1:], Y[1:, :-1]], axis=-1).reshape(n, 4)
+    x1, y1 = np.roll(vx, -1, axis=1), np.roll(vy, -1, axis=1)
+    cr = vx * y1 - x1 * vy
+    area = 0.5 * cr.sum(axis=1)
+    cx = ((vx + x1) * cr).sum(axis=1) / (6.0 * area)
+    cy = ((vy + y1) * cr).sum(axis=1) / (6.0 * area)
+    if np.any(area <= 0):
+        raise ValueError("quad_mesh: cells must be convex and counter-clockwise")
+    C = np.stack([cx, cy, np.full(n, 0.5 * dz)])
+    V = area * dz
+    idx = np.arange(n).reshape(ny, nx)
+    own, nb, S, XF = [], [], [], []
+    # faces between (i, j) and (i+1, j): edge from node (j, i+1) to (j+1, i+1)
+    o = idx[:, :-1].reshape(-1)
+    ax, ay = X[:-1, 1:-1].reshape(-1), Y[:-1, 1:-1].reshape(-1)
+    bx, by = X[1:, 1:-1].reshape(-1), Y[1:, 1:-1].reshape(-1)
+    own.append(o)
+    nb.append(o + 1)
+    S.append(np.stack([(by - ay) * dz, -(bx - ax) * dz, np.zeros(o.size)]))
+    XF.append(np.stack([0.5 * (ax + bx), 0.5 * (ay + by), np.full(o.size, 0.5 * dz)]))
+    # faces between (i, j) and (i, j+1): edge from node (j+1, i) to (j+1, i+1)
+    o = idx[:-1, :].reshape(-1)
+    ax, ay = X[1:-1, :-1].reshape(-1), Y[1:-1, :-1].reshape(-1)
+    bx, by = X[1:-1, 1:].reshape(-1), Y[1:-1, 1:].reshape(-1)
+    own.append(o)
+    nb.append(o + nx)
+    S.append(np.stack([-(by - ay) * dz, (bx - ax) * dz, np.zeros(o.size)]))
+    XF.append(np.stack([0.5 * (ax + bx), 0.5 * (ay + by), np.full(o.size, 0.5 * dz)]))
+    owner = np.concatenate(own)
+    neighbour = np.concatenate(nb)
+    Sf = np.concatenate(S, axis=1)
+    xfc = np.concatenate(XF, axis=1)
+    order = np.lexsort((neighbour, owner))
+    return dict(
+        n=n, F=owner.size,
+        owner=owner[order].astype(np.int32), neighbour=neighbour[order].astype(np.int32),
+        Sf=np.ascontiguousarray(Sf[:, order]), C=C, V=V, xf=np.ascontiguousarray(xfc[:, order]),
+        dims=(nx, ny, 1), spacing=(float(np.diff(X, axis=1).min()), float(np.diff(Y, axis=0).min()), dz),
+        origin=(float(X.min()), float(Y.min()), 0.0),
+    )
+
+
+def wavy_mesh(nx: int, ny: int, lx: float = 2.0, ly: float = 1.0, eps: float = 0.04) -> dict:
+    """A smoothly distorted, non-orthogonal quad mesh of the rectangle
+    [0, lx] x [0, ly] with straight walls: nodes displaced by
+    eps lx sin(pi x/lx) sin(2 pi y/ly) in x and eps ly sin(2 pi x/lx) sin(pi y/ly)
+    in y, an O(1) distortion that does not fade under refinement."""
+    xs, ys = np.linspace(0.0, lx, nx + 1), np.linspace(0.0, ly, ny + 1)
+    x, y = np.meshgrid(xs, ys)
+    X = x + eps * lx * np.sin(math.pi * x / lx) * np.sin(2.0 * math.pi * y / ly)
+    Y = y + eps * ly * np.sin(2.0 * math.pi * x / lx) * np.sin(math.pi * y / ly)
+    return quad_mesh(X, Y, lx / nx)
 
 
 def permute_mesh(mesh: dict, perm: np.ndarray, face_fields=()) -> dict:

@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
 _lib = None
 
 (MUT_NONE, MUT_JUMP_SIGN_EQ15, MUT_LAMBDA_FROM_OWNER, MUT_ARITH_BETA, MUT_DROP_JUMP, MUT_SWAP_ALPHA_DERIV,
- MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ, MUT_GHOST_SWAP_BETA) = range(9)
+ MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ, MUT_GHOST_SWAP_BETA, MUT_NONORTH_SIGN) = range(10)
 KIND_DRY, KIND_WET, KIND_IF_OWNER_WET, KIND_IF_OWNER_DRY = range(4)
 
 
@@ -45,7 +45,7 @@ def _load():
         lib = ct.CDLL(_LIB)
         P = ct.c_void_p
         I, D = ct.c_int, ct.c_double
-        lib.gfm_oracle_faces.argtypes = [I, I, P, P, P, P, P, D, D, P, P, P, P, P, I]
+        lib.gfm_oracle_faces.argtypes = [I, I, P, P, P, P, P, D, D, P, P, P, P, P, P, I]
         lib.gfm_oracle_faces.restype = I
         lib.gfm_oracle_assemble.argtypes = [I, I, P, P, P, P, P, I, D, P, P, P, P, P]
         lib.gfm_oracle_assemble.restype = I
@@ -67,6 +67,8 @@ def _load():
         lib.gfm_oracle_gradient.restype = None
         lib.gfm_oracle_reconstruct.argtypes = [I, I, P, P, P, P, P, P, P]
         lib.gfm_oracle_reconstruct.restype = None
+        lib.gfm_oracle_nonorth.argtypes = [I, I, P, P, P, P, P, P, P, D, D, P, P, P, P, I]
+        lib.gfm_oracle_nonorth.restype = None
         lib.gfm_oracle_set_threads.argtypes = [I]
         lib.gfm_oracle_set_threads.restype = None
         lib.gfm_oracle_max_threads.restype = I
@@ -125,8 +127,9 @@ class System:
         return spmv(self, x)
 
 
-def faces(case, alpha=None, mutate: int = MUT_NONE, C=None) -> Faces:
-    """lambda, gamma, J and the face kind of every internal face (Eqs. 7, 12-18)."""
+def faces(case, alpha=None, mutate: int = MUT_NONE, C=None, rau=None) -> Faces:
+    """lambda, gamma, J and the face kind of every internal face (Eqs. 7, 12-18);
+    gamma carries the face Rhie-Chow coefficient rau when given."""
     lib = _load()
     n, F = case.n, case.F
     alpha = _f64(case.alpha if alpha is None else alpha)
@@ -135,7 +138,8 @@ def faces(case, alpha=None, mutate: int = MUT_NONE, C=None) -> Faces:
     kind = np.empty(F, dtype=np.int8)
     g = _f64(case.g)
     rc = lib.gfm_oracle_faces(n, F, _p(_i32(case.owner)), _p(_i32(case.neighbour)), _p(_f64(case.Sf)), _p(C),
-                              _p(alpha), case.rho_w, case.rho_a, _p(g), _p(lam), _p(gam), _p(jmp), _p(kind),
+                              _p(alpha), case.rho_w, case.rho_a, _p(g),
+                              None if rau is None else _p(_f64(rau)), _p(lam), _p(gam), _p(jmp), _p(kind),
                               int(mutate))
     if rc != 0:
         raise ValueError(f"oracle faces: bad mesh ({rc})")
@@ -256,6 +260,41 @@ def reconstruct(case, phi: np.ndarray, xf=None, use_xf: bool = True) -> np.ndarr
     _load().gfm_oracle_reconstruct(n, F, _p(_i32(case.owner)), _p(_i32(case.neighbour)), _p(_f64(case.C)),
                                    _p(_f64(case.V)), xfp, _p(_f64(phi)), _p(out))
     return out
+
+
+def nonorth_correction(case, p: np.ndarray, rau=None, alpha=None, xf=None, use_xf: bool = True,
+                       mutate: int = MUT_NONE) -> np.ndarray:
+    """Explicit non-orthogonal correction flux corr_f = rau_f k_f . G_f [F]
+    from the gradient of p (see gfm_oracle.c)."""
+    n, F = case.n, case.F
+    alpha = _f64(case.alpha if alpha is None else alpha)
+    if xf is None and use_xf:
+        xf = case.xf
+    out = np.empty(F)
+    _load().gfm_oracle_nonorth(n, F, _p(_i32(case.owner)), _p(_i32(case.neighbour)), _p(_f64(case.Sf)),
+                               _p(_f64(case.C)), _p(_f64(case.V)), None if xf is None else _p(_f64(xf)),
+                               _p(alpha), case.rho_w, case.rho_a, _p(_f64(case.g)),
+                               None if rau is None else _p(_f64(rau)), _p(_f64(p)), _p(out), int(mutate))
+    return out
+
+
+def solve_nonorth(case, correctors: int, rau=None, rtol: float = 1e-13, direct: bool | None = None, phi=None,
+                  mutate: int = MUT_NONE):
+    """Deferred correction: solve with the implicit part, then `correctors`
+    times recompute the explicit non-orthogonal correction from the last
+    p_d and solve again.  Returns (p, corr, Faces, System)."""
+    fc = faces(case, rau=rau)
+    phi = _f64(case.phi if phi is None else phi)
+    if direct is None:
+        direct = case.n <= 1024
+    corr = np.zeros(case.F)
+    p = None
+    for k in range(correctors + 1):
+        sy = assemble(case, fc, phi=phi - corr)
+        p = cholesky_solve(sy) if direct else pcg(sy, rtol=rtol, x0=p)[0]
+        if k < correctors:
+            corr = nonorth_correction(case, p, rau=rau, mutate=mutate)
+    return p, corr, fc, sy
 
 
 def solve(case, rtol: float | None = None, direct: bool | None = None, alpha=None, phi=None, mutate: int = MUT_NONE,
