@@ -283,6 +283,36 @@ gfm_status gfm_gradient(gfm_handle h, const double *p, const double *V, const do
                         const double *phi, double *U, gfm_stream stream);
 
 /*
+ * Real pressure-equation inputs (Sec. 3: the pressure equation comes from
+ * continuity with the Rhie-Chow flux, and its Laplacian is discretised by
+ * the Gauss theorem with an explicit over-relaxed non-orthogonal correction).
+ *
+ * gfm_set_rau: rau [F] (DEVICE, copied; NULL = 1 everywhere) is the face
+ * value of 1/a_P, the inverse diagonal of the momentum equation.  From the
+ * next gfm_assemble on, gamma_f = (c_f / rho_f) * rau_f: the equation is
+ * div(rau beta grad p_d) = div(phi*), with the jump source scaled alike.
+ * Errors: GFM_ERR_NOMEM, GFM_ERR_CUDA.
+ *
+ * gfm_nonorth_correct: after gfm_assemble, splits each area vector into
+ * Delta_f = (S.S)/(S.d) d (the implicit two-point part already assembled)
+ * and k_f = S_f - Delta_f, and adds the explicit part
+ *   corr_f = rau_f k_f . (w_o G_own + (1 - w_o) G_nb),  G = (1/rho) grad p_d
+ * of the given p [n] (gfm_gradient's ghost-value gradient; continuous across
+ * the interface by Eq. 8) to the source: the next gfm_solve solves with
+ * phi* - corr, and its corrected flux is phi* - corr - gamma (p_nb - p_own - J).
+ * Calling it again replaces the correction (deferred correction: solve,
+ * correct from the new p_d, solve again with use_x0).  The next gfm_assemble
+ * clears it.  V [n] volumes (required), xf [3][F] face centres or NULL
+ * (midpoints), corr [F] (nullable) receives the correction flux.  Zero on
+ * orthogonal meshes.  The adjoint treats the correction as a fixed source.
+ * Errors: GFM_ERR_ARG (NULL p or V), GFM_ERR_STATE (before gfm_assemble),
+ * GFM_ERR_NOMEM, GFM_ERR_CUDA.
+ */
+gfm_status gfm_set_rau(gfm_handle h, const double *rau, gfm_stream stream);
+gfm_status gfm_nonorth_correct(gfm_handle h, const double *p, const double *V, const double *xf, double *corr,
+                               gfm_stream stream);
+
+/*
  * Solve without device allocation.  The paper has no counterpart: this is an
  * entry point for callers that cannot call cudaMalloc -- code running inside
  * a host program that owns the GPU's memory (a CFD code or plugin drawing

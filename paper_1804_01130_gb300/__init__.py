@@ -33,7 +33,7 @@ EXPORTED_SYMBOLS = (
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
     "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc", "gfm_autotune",
-    "gfm_partition_tanks", "gfm_gradient",
+    "gfm_partition_tanks", "gfm_gradient", "gfm_set_rau", "gfm_nonorth_correct",
 )
 
 # largest n accepted by gfm_solve_csr_noalloc (its fixed device scratch)
@@ -136,6 +136,8 @@ def load_library(build_if_missing: bool = True):
         "gfm_autotune": ([P, ct.POINTER(_Opts), I, ct.POINTER(_Tuning), ct.POINTER(ct.c_float), P], S),
         "gfm_partition_tanks": ([P, I, I, P, P], S),
         "gfm_gradient": ([P, P, P, P, P, P, P, P], S),
+        "gfm_set_rau": ([P, P, P], S),
+        "gfm_nonorth_correct": ([P, P, P, P, P, P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
     }
@@ -329,6 +331,24 @@ class GFM:
         self._check(self.lib.gfm_gradient(self.h, _ptr(p), _ptr(V), _ptr(xf), _ptr(grad), _ptr(phi), _ptr(U),
                                           _stream(stream)), "gfm_gradient")
         return grad, U
+
+    def set_rau(self, rau=None, stream=None):
+        """Face Rhie-Chow coefficient 1/a_P [F] for the next assemblies (None = 1)."""
+        self._rau = None if rau is None else _f64(rau, self.device)
+        self._check(self.lib.gfm_set_rau(self.h, _ptr(self._rau), _stream(stream)), "gfm_set_rau")
+
+    def nonorth_correct(self, p: torch.Tensor, V, xf=None, return_corr: bool = False, stream=None):
+        """Explicit non-orthogonal correction from p_d into the assembled
+        source (gfm_nonorth_correct); the next solve uses it.  Returns the
+        correction flux [F] when asked."""
+        d = self.device
+        p = _f64(p, d)
+        V = _f64(V, d)
+        xf = None if xf is None else _f64(xf, d).reshape(3, -1).contiguous()
+        corr = torch.empty(self.F, dtype=torch.float64, device=d) if return_corr else None
+        self._check(self.lib.gfm_nonorth_correct(self.h, _ptr(p), _ptr(V), _ptr(xf), _ptr(corr), _stream(stream)),
+                    "gfm_nonorth_correct")
+        return corr
 
     def set_tuning(self, threads=0, ctas_per_sm=0):
         self._check(self.lib.gfm_set_tuning(self.h, ct.byref(_Tuning(int(threads), int(ctas_per_sm)))),

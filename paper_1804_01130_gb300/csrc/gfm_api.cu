@@ -60,6 +60,12 @@ struct gfm_ctx {
     gfm_solve_info *binfos = nullptr, *binfos_h = nullptr;
     // host-buffer entry point staging
     double *stage_alpha = nullptr, *stage_phi = nullptr, *stage_p = nullptr;
+    // real pressure-equation inputs: face Rhie-Chow coefficient, explicit
+    // non-orthogonal correction (allocated on first use)
+    double *rau = nullptr;
+    bool rau_set = false;
+    double *nonorth_corr = nullptr, *phi_eff = nullptr, *grad_scr = nullptr;
+    bool nonorth_active = false;
     // control
     gfm::DevParams *prm = nullptr;
     unsigned *bar = nullptr;
@@ -116,7 +122,8 @@ void free_all(gfm_ctx *h)
                     h->err, h->partials, h->dinfo, h->cc_parent, h->cc_size, h->cc_cand, h->cc_counters,
                     h->cc_bcount, h->cc_boff, h->cc_epart,
                     h->comp, h->cross, h->coarse, h->ftank, h->stank, h->tncell, h->tphys, h->tprm, h->cta,
-                    h->tank_cta, h->binfos, h->tcoff, h->tioff, h->tco};
+                    h->tank_cta, h->binfos, h->tcoff, h->tioff, h->tco, h->rau, h->nonorth_corr, h->phi_eff,
+                    h->grad_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *hptrs[] = {h->hinfo, h->tphys_h, h->tprm_h, h->binfos_h};
@@ -782,7 +789,9 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     fa.kind = h->kind;
     fa.ftank = h->batched ? h->ftank : nullptr;
     fa.tphys = h->batched ? h->tphys : nullptr;
+    fa.rau = h->rau_set ? h->rau : nullptr;
     GFM_CUDA(h, gfm::launch_faces(fa, s));
+    h->nonorth_active = false;
     gfm::CellArgs ca;
     ca.m = sell_of(h);
     ca.gamma = h->gamma;
@@ -887,7 +896,8 @@ gfm_status gfm_solve(gfm_handle h, const gfm_solve_opts *opts, double *p, double
     st = enqueue_solve(h, opts, h->b, p, opts->use_x0, idev, s);
     if (st != GFM_OK) return st;
     if (phi_corr) {
-        GFM_CUDA(h, gfm::launch_corrected_flux(h->F, h->owner, h->neighbour, h->gamma, h->jump, h->phi, p, phi_corr, s));
+        GFM_CUDA(h, gfm::launch_corrected_flux(h->F, h->owner, h->neighbour, h->gamma, h->jump,
+                                               h->nonorth_active ? h->phi_eff : h->phi, p, phi_corr, s));
         h->prof.launches += 1;
         h->prof.launches_total += 1;
     }
@@ -1008,6 +1018,104 @@ gfm_status gfm_gradient(gfm_handle h, const double *p, const double *V, const do
     GFM_CUDA(h, gfm::launch_gradient(a, s));
     h->prof.launches = 1;
     h->prof.launches_total += 1;
+    return GFM_OK;
+}
+
+gfm_status gfm_set_rau(gfm_handle h, const double *rau, gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    clear_stale_error();
+    if (!rau) {
+        h->rau_set = false;
+        return GFM_OK;
+    }
+    if (!h->rau) {
+        cudaError_t e = dalloc(&h->rau, (size_t)h->F);
+        if (e != cudaSuccess) return fail(h, GFM_ERR_NOMEM, "allocating the face coefficient");
+    }
+    GFM_CUDA(h, cudaMemcpyAsync(h->rau, rau, sizeof(double) * h->F, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    h->rau_set = true;
+    return GFM_OK;
+}
+
+gfm_status gfm_nonorth_correct(gfm_handle h, const double *p, const double *V, const double *xf, double *corr,
+                               gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    if (!p || !V) return fail(h, GFM_ERR_ARG, "p and V must be non-NULL");
+    if (!h->assembled) return fail(h, GFM_ERR_STATE, "non-orthogonal correction before assemble");
+    clear_stale_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->grad_scr) {
+        cudaError_t e = dalloc(&h->grad_scr, 3 * (size_t)h->n);
+        if (e == cudaSuccess) e = dalloc(&h->nonorth_corr, (size_t)h->F);
+        if (e == cudaSuccess) e = dalloc(&h->phi_eff, (size_t)h->F);
+        if (e != cudaSuccess) return fail(h, GFM_ERR_NOMEM, "allocating the correction workspace");
+    }
+    gfm::GradArgs ga{};
+    ga.m = sell_of(h);
+    ga.n = h->n;
+    ga.F = h->F;
+    ga.iperm = h->iperm;
+    ga.owner = h->owner;
+    ga.neighbour = h->neighbour;
+    ga.Sf = h->Sf;
+    ga.C = h->C;
+    ga.V = V;
+    ga.xf = xf;
+    ga.lambda = h->lambda;
+    ga.jump = h->jump;
+    ga.p = p;
+    ga.rho_w = h->phys.rho_w;
+    ga.rho_a = h->phys.rho_a;
+    ga.stank = h->batched ? h->stank : nullptr;
+    ga.tphys = h->batched ? h->tphys : nullptr;
+    ga.grad = h->grad_scr;
+    GFM_CUDA(h, gfm::launch_gradient(ga, s));
+    gfm::NonorthArgs na{};
+    na.n = h->n;
+    na.F = h->F;
+    na.owner = h->owner;
+    na.neighbour = h->neighbour;
+    na.Sf = h->Sf;
+    na.C = h->C;
+    na.xf = xf;
+    na.rau = h->rau_set ? h->rau : nullptr;
+    na.G = h->grad_scr;
+    na.phi = h->phi;
+    na.gamma = h->gamma;
+    na.jump = h->jump;
+    na.corr = h->nonorth_corr;
+    na.phi_eff = h->phi_eff;
+    na.sigma = h->sigma;
+    GFM_CUDA(h, gfm::launch_nonorth(na, s));
+    // the cell sums again: b from the corrected sigma (diag and the tables
+    // are rewritten with the same values)
+    gfm::CellArgs ca;
+    ca.m = sell_of(h);
+    ca.gamma = h->gamma;
+    ca.sigma = h->sigma;
+    ca.ref = h->ref_internal;
+    ca.ref_value = h->phys.ref_value;
+    ca.b = h->b;
+    ca.diag = h->diag;
+    ca.dinv = h->dinv;
+    ca.dinv32 = h->dinv32;
+    ca.prm = h->prm;
+    ca.iperm = h->iperm;
+    ca.stank = h->batched ? h->stank : nullptr;
+    ca.tphys = h->batched ? h->tphys : nullptr;
+    ca.tprm = h->batched ? h->tprm : nullptr;
+    GFM_CUDA(h, gfm::launch_cells(ca, s));
+    int launched = 3;
+    if (h->ref_internal < 0) {
+        GFM_CUDA(h, gfm::launch_bsums(h->b, h->n, h->prm, s));
+        ++launched;
+    }
+    if (corr) GFM_CUDA(h, cudaMemcpyAsync(corr, h->nonorth_corr, sizeof(double) * h->F, cudaMemcpyDeviceToDevice, s));
+    h->nonorth_active = true;
+    h->prof.launches = launched;
+    h->prof.launches_total += launched;
     return GFM_OK;
 }
 

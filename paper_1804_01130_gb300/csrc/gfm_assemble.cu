@@ -18,6 +18,7 @@ enum : int8_t { kDry = 0, kWet = 1, kIfOwnerWet = 2, kIfOwnerDry = 3 };
 //   lambda = (alpha_W - 0.5) / (alpha_W - alpha_D)                 Eq. 13
 //   c      = (S.S) / (S.d),  d = C_nb - C_own
 //   gamma  = c / (lambda rho_w + (1 - lambda) rho_a)  = c beta+ beta- / beta_w   Eqs. 16-18, 20
+//            (times the face Rhie-Chow coefficient rau_f when one is set)
 //   x_G    = C_W + lambda (C_D - C_W)                              Eq. 12
 //   H      = (rho_w - rho_a) g.x_G  = p_d(dry) - p_d(wet)           Eq. 7
 //   J      = +H (owner wet) / -H (owner dry) / 0 (no interface)
@@ -59,7 +60,8 @@ __global__ void k_faces(FaceArgs a)
     const double dz = a.C[2 * n + nb] - a.C[2 * n + o];
     const double c = (Sx * Sx + Sy * Sy + Sz * Sz) / (Sx * dx + Sy * dy + Sz * dz);
     const double rf = lam * rho_w + (1.0 - lam) * rho_a;
-    const double gam = c / rf;
+    double gam = c / rf;
+    if (a.rau) gam = gam * a.rau[f];  // face Rhie-Chow coefficient 1/a_P
     double J = 0.0;
     if (kind >= kIfOwnerWet) {
         const double xg0 = a.C[W] + lam * (a.C[D] - a.C[W]);

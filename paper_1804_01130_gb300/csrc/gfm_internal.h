@@ -138,6 +138,7 @@ struct FaceArgs {
     int8_t *kind;
     const int32_t *ftank;    // batched: tank of each face (else nullptr)
     const TankPhys *tphys;   // batched: physics per tank
+    const double *rau;       // face Rhie-Chow coefficient 1/a_P (nullptr = 1)
 };
 cudaError_t launch_faces(const FaceArgs &a, cudaStream_t s);
 
@@ -216,6 +217,20 @@ struct GradArgs {
     double *grad, *U;                  // [3][n] caller order, either nullable
 };
 cudaError_t launch_gradient(const GradArgs &a, cudaStream_t s);
+
+// Explicit non-orthogonal correction: corr_f = rau_f k_f . G_f from the
+// cell gradient G [3][n] (caller order), phi_eff = phi - corr and
+// sigma = phi_eff + gamma J for the cell sums.
+struct NonorthArgs {
+    int32_t n, F;
+    const int32_t *owner, *neighbour;
+    const double *Sf, *C, *xf;  // xf nullable
+    const double *rau;          // nullable
+    const double *G;
+    const double *phi, *gamma, *jump;
+    double *corr, *phi_eff, *sigma;
+};
+cudaError_t launch_nonorth(const NonorthArgs &a, cudaStream_t s);
 
 cudaError_t launch_gather(const double *src_user, const int32_t *iperm, double *dst_internal, int32_t n,
                           int32_t n_pad, cudaStream_t s);
