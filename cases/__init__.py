@@ -68,6 +68,8 @@ class Case:
     mode: str = "fp64"
     dims: tuple = ()
     meta: dict = field(default_factory=dict)
+    fv_ptr: np.ndarray | None = None  # int32 [F+1] face polygons: vertices of face f are
+    fv_xyz: np.ndarray | None = None  # float64 [3, nv] columns fv_ptr[f]..fv_ptr[f+1]-1, in order round it
 
     @property
     def faces_per_cell(self) -> float:
@@ -146,7 +148,7 @@ def graded_mesh(xn, yn, zn) -> dict:
     C[1] = 0.5 * (yn[j] + yn[j + 1])
     C[2] = 0.5 * (zn[k] + zn[k + 1])
     V = dxs[i] * dys[j] * dzs[k]
-    own, nb, S, XF = [], [], [], []
+    own, nb, S, XF, PV = [], [], [], [], []
     for axis, step, ok in ((0, 1, i < nx - 1), (1, nx, j < ny - 1), (2, nx * ny, k < nz - 1)):
         o = idx[ok]
         if o.size == 0:
@@ -154,6 +156,18 @@ def graded_mesh(xn, yn, zn) -> dict:
         io, jo, ko = i[ok], j[ok], k[ok]
         s = np.zeros((3, o.size))
         xf = C[:, o].copy()
+        # the face's four corners, in order round it
+        lo = np.stack([xn[io], yn[jo], zn[ko]])
+        hi = np.stack([xn[io + 1], yn[jo + 1], zn[ko + 1]])
+        a, b = [q for q in range(3) if q != axis]
+        corners = []
+        for ca, cb in ((0, 0), (1, 0), (1, 1), (0, 1)):
+            v = np.empty((3, o.size))
+            v[axis] = hi[axis]
+            v[a] = hi[a] if ca else lo[a]
+            v[b] = hi[b] if cb else lo[b]
+            corners.append(v)
+        PV.append(np.stack(corners, axis=1))  # [3, 4, m]
         if axis == 0:
             s[0] = dys[jo] * dzs[ko]
             xf[0] = xn[io + 1]
@@ -171,13 +185,17 @@ def graded_mesh(xn, yn, zn) -> dict:
     neighbour = np.concatenate(nb)
     Sf = np.concatenate(S, axis=1)
     xfc = np.concatenate(XF, axis=1)
+    pv = np.concatenate(PV, axis=2)
     order = np.lexsort((neighbour, owner))
+    F = owner.size
     return dict(
-        n=n, F=owner.size,
+        n=n, F=F,
         owner=owner[order].astype(np.int32), neighbour=neighbour[order].astype(np.int32),
         Sf=np.ascontiguousarray(Sf[:, order]), C=C, V=V, xf=np.ascontiguousarray(xfc[:, order]),
         dims=(nx, ny, nz), spacing=(float(dxs.min()), float(dys.min()), float(dzs.min())),
         origin=(float(xn[0]), float(yn[0]), float(zn[0])),
+        fv_ptr=np.arange(0, 4 * F + 1, 4, dtype=np.int32),
+        fv_xyz=np.ascontiguousarray(pv[:, :, order].transpose(0, 2, 1).reshape(3, 4 * F)),
     )
 
 
@@ -205,7 +223,13 @@ def quad_mesh(X, Y, dz: float) -> dict:
     C = np.stack([cx, cy, np.full(n, 0.5 * dz)])
     V = area * dz
     idx = np.arange(n).reshape(ny, nx)
-    own, nb, S, XF = [], [], [], []
+    own, nb, S, XF, PV = [], [], [], [], []
+
+    def edge_polygon(ax, ay, bx, by):  # the edge extruded over [0, dz]: 4 corners in order
+        z0, z1 = np.zeros(ax.size), np.full(ax.size, dz)
+        return np.stack([np.stack([ax, ay, z0]), np.stack([bx, by, z0]), np.stack([bx, by, z1]),
+                         np.stack([ax, ay, z1])], axis=1)
+
     # faces between (i, j) and (i+1, j): edge from node (j, i+1) to (j+1, i+1)
     o = idx[:, :-1].reshape(-1)
     ax, ay = X[:-1, 1:-1].reshape(-1), Y[:-1, 1:-1].reshape(-1)
@@ -214,6 +238,7 @@ def quad_mesh(X, Y, dz: float) -> dict:
     nb.append(o + 1)
     S.append(np.stack([(by - ay) * dz, -(bx - ax) * dz, np.zeros(o.size)]))
     XF.append(np.stack([0.5 * (ax + bx), 0.5 * (ay + by), np.full(o.size, 0.5 * dz)]))
+    PV.append(edge_polygon(ax, ay, bx, by))
     # faces between (i, j) and (i, j+1): edge from node (j+1, i) to (j+1, i+1)
     o = idx[:-1, :].reshape(-1)
     ax, ay = X[1:-1, :-1].reshape(-1), Y[1:-1, :-1].reshape(-1)
@@ -222,17 +247,22 @@ def quad_mesh(X, Y, dz: float) -> dict:
     nb.append(o + nx)
     S.append(np.stack([-(by - ay) * dz, (bx - ax) * dz, np.zeros(o.size)]))
     XF.append(np.stack([0.5 * (ax + bx), 0.5 * (ay + by), np.full(o.size, 0.5 * dz)]))
+    PV.append(edge_polygon(ax, ay, bx, by))
     owner = np.concatenate(own)
     neighbour = np.concatenate(nb)
     Sf = np.concatenate(S, axis=1)
     xfc = np.concatenate(XF, axis=1)
+    pv = np.concatenate(PV, axis=2)
     order = np.lexsort((neighbour, owner))
+    F = owner.size
     return dict(
-        n=n, F=owner.size,
+        n=n, F=F,
         owner=owner[order].astype(np.int32), neighbour=neighbour[order].astype(np.int32),
         Sf=np.ascontiguousarray(Sf[:, order]), C=C, V=V, xf=np.ascontiguousarray(xfc[:, order]),
         dims=(nx, ny, 1), spacing=(float(np.diff(X, axis=1).min()), float(np.diff(Y, axis=0).min()), dz),
         origin=(float(X.min()), float(Y.min()), 0.0),
+        fv_ptr=np.arange(0, 4 * F + 1, 4, dtype=np.int32),
+        fv_xyz=np.ascontiguousarray(pv[:, :, order].transpose(0, 2, 1).reshape(3, 4 * F)),
     )
 
 
@@ -276,6 +306,17 @@ def permute_mesh(mesh: dict, perm: np.ndarray, face_fields=()) -> dict:
         xf=np.ascontiguousarray(mesh["xf"][:, order]), perm=perm,
     )
     out["fields"] = [np.ascontiguousarray((np.asarray(ff) * sign)[order]) for ff in face_fields]
+    if mesh.get("fv_xyz") is not None:  # equal-size polygons: reorder them with the faces
+        ptr = np.asarray(mesh["fv_ptr"])
+        nvf = np.diff(ptr)
+        if np.all(nvf == nvf[0]):
+            k = int(nvf[0])
+            out["fv_xyz"] = np.ascontiguousarray(
+                mesh["fv_xyz"].reshape(3, -1, k)[:, order, :].reshape(3, -1))
+            out["fv_ptr"] = ptr
+        else:
+            out.pop("fv_xyz")
+            out.pop("fv_ptr")
     return out
 
 
@@ -443,7 +484,8 @@ def _case_from(mesh, alpha, phi, name, ref_ijk, **kw) -> Case:
         ref = int(mesh["perm"][ref])
     return Case(name=name, n=mesh["n"], F=mesh["F"], owner=mesh["owner"], neighbour=mesh["neighbour"],
                 Sf=mesh["Sf"], C=mesh["C"], V=mesh["V"], xf=mesh["xf"], alpha=np.ascontiguousarray(alpha),
-                phi=np.ascontiguousarray(phi), ref_cell=int(ref), dims=mesh["dims"], **kw)
+                phi=np.ascontiguousarray(phi), ref_cell=int(ref), dims=mesh["dims"],
+                fv_ptr=mesh.get("fv_ptr"), fv_xyz=mesh.get("fv_xyz"), **kw)
 
 
 def _wave_tank(nx, ny, lx, ly, depth, ka, nwaves, seed, name, rtol, mode, thickness=None) -> Case:

@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
 _lib = None
 
 (MUT_NONE, MUT_JUMP_SIGN_EQ15, MUT_LAMBDA_FROM_OWNER, MUT_ARITH_BETA, MUT_DROP_JUMP, MUT_SWAP_ALPHA_DERIV,
- MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ, MUT_GHOST_SWAP_BETA, MUT_NONORTH_SIGN) = range(10)
+ MUT_PCG_NO_PRECOND, MUT_PCG_STALE_RZ, MUT_GHOST_SWAP_BETA, MUT_NONORTH_SIGN, MUT_ISO_DOWNWIND) = range(11)
 KIND_DRY, KIND_WET, KIND_IF_OWNER_WET, KIND_IF_OWNER_DRY = range(4)
 
 
@@ -69,6 +69,10 @@ def _load():
         lib.gfm_oracle_reconstruct.restype = None
         lib.gfm_oracle_nonorth.argtypes = [I, I, P, P, P, P, P, P, P, D, D, P, P, P, P, I]
         lib.gfm_oracle_nonorth.restype = None
+        lib.gfm_oracle_iso_flux.argtypes = [I, I, P, P, P, P, D, P, P, I, P, P, P, P, P, P, P, I]
+        lib.gfm_oracle_iso_flux.restype = None
+        lib.gfm_oracle_iso_advect.argtypes = [I, I, P, P, P, P, P, P]
+        lib.gfm_oracle_iso_advect.restype = None
         lib.gfm_oracle_set_threads.argtypes = [I]
         lib.gfm_oracle_set_threads.restype = None
         lib.gfm_oracle_max_threads.restype = I
@@ -295,6 +299,30 @@ def solve_nonorth(case, correctors: int, rau=None, rtol: float = 1e-13, direct: 
         if k < correctors:
             corr = nonorth_correction(case, p, rau=rau, mutate=mutate)
     return p, corr, fc, sy
+
+
+def iso_flux(case, phi, dt: float, fv_ptr, fv_xyz, has_iso, xS, nS, UnS, alpha=None, xf=None,
+             mutate: int = MUT_NONE):
+    """isoAdvector face fluxes (Sec. 3.2): returns (I_f = int alpha_f+ dtau, dV_f = phi_f I_f)."""
+    n, F = case.n, case.F
+    alpha = _f64(case.alpha if alpha is None else alpha)
+    fv_xyz = _f64(fv_xyz).reshape(3, -1)
+    I, dV = np.empty(F), np.empty(F)
+    _load().gfm_oracle_iso_flux(n, F, _p(_i32(case.owner)), _p(_i32(case.neighbour)), _p(alpha), _p(_f64(phi)),
+                                float(dt), _p(_i32(fv_ptr)), _p(np.ascontiguousarray(fv_xyz)), int(fv_xyz.shape[1]),
+                                _p(_f64(case.xf if xf is None else xf)),
+                                _p(np.ascontiguousarray(has_iso, dtype=np.int8)), _p(_f64(xS)), _p(_f64(nS)),
+                                _p(_f64(UnS)), _p(I), _p(dV), int(mutate))
+    return I, dV
+
+
+def iso_advect(case, dV, alpha=None) -> np.ndarray:
+    """alpha after the step: alpha - (1/V) sum_f s_f dV_f."""
+    out = np.empty(case.n)
+    alpha = _f64(case.alpha if alpha is None else alpha)
+    _load().gfm_oracle_iso_advect(case.n, case.F, _p(_i32(case.owner)), _p(_i32(case.neighbour)),
+                                  _p(_f64(case.V)), _p(alpha), _p(_f64(dV)), _p(out))
+    return out
 
 
 def solve(case, rtol: float | None = None, direct: bool | None = None, alpha=None, phi=None, mutate: int = MUT_NONE,
