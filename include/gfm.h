@@ -380,6 +380,91 @@ gfm_status gfm_solve_csr_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr,
 gfm_status gfm_partition_tanks(const int64_t *cells, int32_t n_tanks, int32_t n_ranks, int32_t *rank_of_tank,
                                int64_t *rank_cells);
 
+/*
+ * The pressure part of one time step of the segregated solver (Sec. 3,
+ * flow chart: SIMPLE outer iterations around PISO correctors; Sec. 4.1.1
+ * uses 6 outer iterations with 2 pressure correctors each), enqueued as one
+ * stream-ordered sequence that a CUDA graph can capture and replay:
+ *   for k = 0 .. n_solves-1:
+ *     gfm_assemble(alpha, phi_star + k F)    the corrector's predicted flux
+ *     gfm_solve into p, warm-started from the previous corrector's p_d
+ *       (k = 0: from p when opts->use_x0), info + k (DEVICE records)
+ *     n_nonorth times: gfm_nonorth_correct from the new p_d, solve again
+ *   then, for the last corrector: phi_corr [F] (nullable) = corrected flux,
+ *   grad [3][n] (nullable) = (1/rho) grad p_d, U [3][n] (nullable, needs
+ *   phi_corr) = cell velocity from phi_corr (gfm_gradient).
+ * alpha [n] is the step's volume fraction (one advection per time step),
+ * phi_star [n_solves][F] the predicted fluxes (the momentum predictor's
+ * Rhie-Chow fluxes, produced outside this library), phys as gfm_assemble.
+ * opts->info_on_device must be 1: the call never synchronises; info holds
+ * n_solves records (n_solves x n_tanks on a batched handle).  V [n] and xf
+ * [3][F] (nullable) as gfm_gradient; V is required for n_nonorth > 0, grad
+ * or U.  Errors: those of the calls it makes, GFM_ERR_ARG.
+ */
+gfm_status gfm_piso_step(gfm_handle h, const gfm_solve_opts *opts, int32_t n_solves, int32_t n_nonorth,
+                         const double *alpha, const double *phi_star, const gfm_phys *phys, double *p, double *phi_corr,
+                         const double *V, const double *xf, double *grad, double *U, gfm_solve_info *info,
+                         gfm_stream stream);
+
+/*
+ * isoAdvector advection step (Sec. 3.2) on the handle's mesh: the volume of
+ * heavy fluid each face passes during [t, t + dt] and the volume-fraction
+ * update,
+ *   dV_f = phi_f int_0^dt alpha_f+(tau) dtau                     (Eq. dV)
+ *   alpha_P(t + dt) = alpha_P(t) - 1/V_P sum_f s_Pf dV_f,
+ * alpha_f+ being the submerged fraction of the face (Eq. alphaf).  In the
+ * upwind cell U of face f (owner when phi_f >= 0) the interface is the
+ * isoface plane through xS [3][n] (column U) with unit normal nS [3][n]
+ * pointing away from the heavy fluid, moving at normal speed UnS [n]
+ * (= U_S.n_S); it reaches a point x at t + (x - x_S).n_S / UnS (Eq. tv).
+ * The face surface is the union of the triangles (xf, v_k, v_k+1) over its
+ * polygon, fv_xyz [3][nvt] columns fv_ptr[f] .. fv_ptr[f+1]-1 (in order
+ * round the face; fv_ptr int32 [F+1]).  Each triangle is swept in the
+ * paper's way: vertex times in order, the cut point x4 (Eq. x_41), the two
+ * quadratic pieces of the swept fraction (Eqs. aplus1, aplus2) and their
+ * exact time integrals (Eq. intaplus).  UnS < 0 (interface moving into the
+ * heavy fluid): the submerged fraction is the complement of the swept one;
+ * UnS = 0: a static plane.  A face whose upwind cell has has_iso [n]
+ * (int8) = 0 carries alpha_U throughout.  The isofaces (the reconstruction
+ * step) are inputs.  Outputs: dV [F]; integral [F] (nullable) the time
+ * integrals; alpha_new [n] (nullable; needs V [n]).  Face arrays in the
+ * caller's face order, cell arrays in the caller's cell order.  FP64, one
+ * thread per face, then one per cell summing its faces in ascending order.
+ * Errors: GFM_ERR_ARG (NULL, dt < 0, nvt < 3), GFM_ERR_CUDA.
+ */
+gfm_status gfm_iso_advect(gfm_handle h, const double *alpha, const double *phi, double dt, const int32_t *fv_ptr,
+                          const double *fv_xyz, int32_t nvt, const double *xf, const int8_t *has_iso,
+                          const double *xS, const double *nS, const double *UnS, const double *V, double *integral,
+                          double *dV, double *alpha_new, gfm_stream stream);
+
+/*
+ * Operator-table format of the streamed mixed-precision pass.  When a
+ * CTA's slice tables do not fit in shared memory, the operator pass streams
+ * them every iteration; the full form is 8 bytes per slot (neighbour index,
+ * FP32 coefficient).  The compact form is 4 bytes: the neighbour as a signed
+ * 16-bit offset from the slot's own cell and a 16-bit code of the
+ * coefficient -- off the interface, one of the two values (c_f/rho_w,
+ * c_f/rho_a) of the face's class of bit-identical c_f = S.S/S.d, looked up
+ * in a dictionary staged in shared memory; at an interface face an escape
+ * code sends the pass to the FP32 coefficient in global memory.  Both forms
+ * give bit-identical results.  The compact form is usable when every
+ * neighbour offset fits 16 bits (after renumbering) and the faces fall into
+ * at most 2047 classes; it is not used while a face Rhie-Chow coefficient
+ * is set (gfm_set_rau), which makes every coefficient distinct.
+ * gfm_set_table: compact = 1 uses it when usable, 0 (default) never;
+ * force_stream = 1 streams the tables even when they would fit in shared
+ * memory (for tests and tuning; default 0).  Takes effect at the next solve.
+ * The compact form halves the streamed bytes, but the operator pass of the
+ * meshes measured here is bound by gather latency rather than by its share
+ * of HBM bandwidth, and interface slots add a dependent load: it was slower
+ * on the 3D box and the 64-tank batch, hence off by default.
+ * gfm_get_table (host pointers, any may be NULL): whether the compact form
+ * is usable for this mesh, its number of classes, and whether the last
+ * assembly wrote it.
+ */
+gfm_status gfm_set_table(gfm_handle h, int32_t compact, int32_t force_stream);
+gfm_status gfm_get_table(gfm_handle h, int32_t *compact_usable, int32_t *n_classes, int32_t *compact_valid);
+
 /* Launch shape of the persistent kernels (threads a multiple of 32, at most
  * 512).  threads = 0 / ctas_per_sm = 0 keep the current value.  Errors:
  * GFM_ERR_ARG if the shape is out of range or cannot be co-resident. */

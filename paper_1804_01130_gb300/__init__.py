@@ -33,7 +33,8 @@ EXPORTED_SYMBOLS = (
     "gfm_solve_adjoint", "gfm_solve_host", "gfm_set_tuning", "gfm_get_tuning", "gfm_set_profiling",
     "gfm_get_profile", "gfm_get_sizes", "gfm_get_permutation", "gfm_status_string", "gfm_last_error",
     "gfm_set_coarse", "gfm_get_coarse", "gfm_create_batched", "gfm_solve_csr_noalloc", "gfm_autotune",
-    "gfm_partition_tanks", "gfm_gradient", "gfm_set_rau", "gfm_nonorth_correct",
+    "gfm_partition_tanks", "gfm_gradient", "gfm_set_rau", "gfm_nonorth_correct", "gfm_set_table",
+    "gfm_get_table", "gfm_piso_step", "gfm_iso_advect",
 )
 
 # largest n accepted by gfm_solve_csr_noalloc (its fixed device scratch)
@@ -137,6 +138,10 @@ def load_library(build_if_missing: bool = True):
         "gfm_partition_tanks": ([P, I, I, P, P], S),
         "gfm_gradient": ([P, P, P, P, P, P, P, P], S),
         "gfm_set_rau": ([P, P, P], S),
+        "gfm_set_table": ([P, I, I], S),
+        "gfm_iso_advect": ([P, P, P, ct.c_double, P, P, I, P, P, P, P, P, P, P, P, P, P], S),
+        "gfm_piso_step": ([P, ct.POINTER(_Opts), I, I, P, P, ct.POINTER(_Phys), P, P, P, P, P, P, P, P], S),
+        "gfm_get_table": ([P, ct.POINTER(I), ct.POINTER(I), ct.POINTER(I)], S),
         "gfm_nonorth_correct": ([P, P, P, P, P, P], S),
         "gfm_status_string": ([S], ct.c_char_p),
         "gfm_last_error": ([P], ct.c_char_p),
@@ -331,6 +336,72 @@ class GFM:
         self._check(self.lib.gfm_gradient(self.h, _ptr(p), _ptr(V), _ptr(xf), _ptr(grad), _ptr(phi), _ptr(U),
                                           _stream(stream)), "gfm_gradient")
         return grad, U
+
+    def piso_step(self, alpha, phi_star: torch.Tensor, p: torch.Tensor, info: torch.Tensor, V=None, xf=None,
+                  n_nonorth: int = 0, phi_corr: torch.Tensor | None = None, grad: torch.Tensor | None = None,
+                  U: torch.Tensor | None = None, mode="mixed", rtol=1e-10, inner_rtol=1e-4, use_x0=False,
+                  rho_w=1000.0, rho_a=1.0, g=(0.0, -9.81, 0.0), ref_cell=0, ref_value=0.0, timeout_ms=2000.0,
+                  stream=None):
+        """Enqueue the pressure part of one time step (gfm_piso_step):
+        phi_star [n_solves, F] predicted fluxes, p [n] solution (x0 when
+        use_x0), info a float64 device tensor of 4 * n_solves entries (the
+        records), optional outputs phi_corr [F], grad and U [3, n].  Nothing
+        is synchronised, so the call can be captured in a CUDA graph; every
+        tensor must already be on the device."""
+        for t in (alpha, phi_star, p, info):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda):
+                raise GFMError(GFM_ERR_ARG, "piso_step takes device tensors")
+        n_solves = int(phi_star.shape[0]) if phi_star.dim() == 2 else int(phi_star.numel() // self.F)
+        if phi_star.numel() != n_solves * self.F or n_solves < 1:
+            raise GFMError(GFM_ERR_ARG, f"phi_star must hold n_solves x {self.F} values")
+        if info.numel() * info.element_size() < 32 * n_solves:
+            raise GFMError(GFM_ERR_ARG, f"info needs {32 * n_solves} bytes")
+        self.phys = self.make_phys(rho_w, rho_a, g, ref_cell, ref_value)
+        o = self.make_opts(mode, rtol, inner_rtol, 1_000_000, 30, use_x0, True, timeout_ms)
+        self._check(self.lib.gfm_piso_step(self.h, ct.byref(o), n_solves, int(n_nonorth), _ptr(alpha),
+                                           _ptr(phi_star), ct.byref(self.phys), _ptr(p), _ptr(phi_corr), _ptr(V),
+                                           _ptr(xf), _ptr(grad), _ptr(U), _ptr(info), _stream(stream)),
+                    "gfm_piso_step")
+
+    def iso_advect(self, alpha, phi, dt: float, fv_ptr, fv_xyz, xf, has_iso, xS, nS, UnS, V=None,
+                   stream=None):
+        """isoAdvector step (gfm_iso_advect): returns (dV [F], integral [F],
+        alpha_new [n] or None without V).  Inputs are array-likes, copied to
+        the device."""
+        d = self.device
+        alpha, phi = _f64(alpha, d), _f64(phi, d)
+        fv_ptr = _i32(fv_ptr, d)
+        fv_xyz = _f64(fv_xyz, d).reshape(3, -1).contiguous()
+        xf = _f64(xf, d).reshape(3, -1).contiguous()
+        has = torch.as_tensor(has_iso).to(device=d, dtype=torch.int8).contiguous()
+        xS = _f64(xS, d).reshape(3, -1).contiguous()
+        nS = _f64(nS, d).reshape(3, -1).contiguous()
+        UnS = _f64(UnS, d)
+        V = None if V is None else _f64(V, d)
+        dV = torch.empty(self.F, dtype=torch.float64, device=d)
+        integral = torch.empty(self.F, dtype=torch.float64, device=d)
+        a_new = torch.empty(self.n, dtype=torch.float64, device=d) if V is not None else None
+        self._check(self.lib.gfm_iso_advect(self.h, _ptr(alpha), _ptr(phi), float(dt), _ptr(fv_ptr), _ptr(fv_xyz),
+                                            int(fv_xyz.shape[1]), _ptr(xf), _ptr(has), _ptr(xS), _ptr(nS),
+                                            _ptr(UnS), _ptr(V), _ptr(integral), _ptr(dV), _ptr(a_new),
+                                            _stream(stream)), "gfm_iso_advect")
+        return dV, integral, a_new
+
+    def infos_of_step(self, info: torch.Tensor, n_solves: int):
+        """The n_solves records a piso_step wrote."""
+        raw = info.detach().cpu().numpy().tobytes()[:32 * n_solves]
+        rec = (_Info * n_solves).from_buffer_copy(raw)
+        return [SolveInfo(i.iters, i.refinements, i.status, i.rel_res_l2, i.rel_res_l1) for i in rec]
+
+    def set_table(self, compact: bool = False, force_stream: bool = False):
+        """Operator-table format of the streamed mixed pass (gfm_set_table)."""
+        self._check(self.lib.gfm_set_table(self.h, int(bool(compact)), int(bool(force_stream))), "gfm_set_table")
+
+    def table_info(self) -> dict:
+        """{'compact_usable', 'classes', 'compact_valid'} (gfm_get_table)."""
+        u, k, v = ct.c_int32(), ct.c_int32(), ct.c_int32()
+        self._check(self.lib.gfm_get_table(self.h, ct.byref(u), ct.byref(k), ct.byref(v)), "gfm_get_table")
+        return {"compact_usable": bool(u.value), "classes": k.value, "compact_valid": bool(v.value)}
 
     def set_rau(self, rau=None, stream=None):
         """Face Rhie-Chow coefficient 1/a_P [F] for the next assemblies (None = 1)."""

@@ -30,6 +30,7 @@ UNITS = {
     "gfm_noalloc.cu": ["-Xptxas", "-v"],
     "gfm_shard.cpp": [],
     "gfm_gradient.cu": [],
+    "gfm_iso.cu": [],
 }
 HEADERS = ["gfm_internal.h", "gfm_setup.h"]
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "gfm_internal.h"
@@ -66,6 +67,17 @@ struct gfm_ctx {
     bool rau_set = false;
     double *nonorth_corr = nullptr, *phi_eff = nullptr, *grad_scr = nullptr;
     bool nonorth_active = false;
+    // compact operator table for the streamed mixed pass (see Sell::ent):
+    // usable when every neighbour offset fits 16 bits and the faces fall
+    // into at most (kMaxDict - 1) / 2 classes of bit-identical c_f
+    bool ct_ok = false, ent_valid = false;
+    bool ct_pref = false;       // gfm_set_table: use the compact table when usable (off by default)
+    bool force_stream = false;  // gfm_set_table: stream the tables even when they fit
+    int n_cls = 0;
+    uint32_t *ent = nullptr;
+    int32_t *fcls = nullptr, *ctank = nullptr;
+    double *ccls = nullptr;
+    float *dict = nullptr;
     // control
     gfm::DevParams *prm = nullptr;
     unsigned *bar = nullptr;
@@ -123,7 +135,7 @@ void free_all(gfm_ctx *h)
                     h->cc_bcount, h->cc_boff, h->cc_epart,
                     h->comp, h->cross, h->coarse, h->ftank, h->stank, h->tncell, h->tphys, h->tprm, h->cta,
                     h->tank_cta, h->binfos, h->tcoff, h->tioff, h->tco, h->rau, h->nonorth_corr, h->phi_eff,
-                    h->grad_scr};
+                    h->grad_scr, h->ent, h->fcls, h->ctank, h->ccls, h->dict};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *hptrs[] = {h->hinfo, h->tphys_h, h->tprm_h, h->binfos_h};
@@ -145,6 +157,9 @@ gfm::Sell sell_of(gfm_ctx *h)
     m.face = h->face;
     m.val64 = h->val64;
     m.val32 = h->val32;
+    m.ent = h->ent_valid ? h->ent : nullptr;
+    m.dict = h->dict;
+    m.n_dict = 2 * h->n_cls + 1;
     return m;
 }
 
@@ -166,6 +181,7 @@ gfm_status check_opts(gfm_ctx *h, const gfm_solve_opts *o)
 struct LaunchPlan {
     int grid = 0, threads = 0, cache_cap = 0, meta_slots = 0;
     int n_stages = 0, stage_slices = 0, stage_cap = 0;  // streamed tables (MIXED), 0 = not streamed
+    bool ct = false;                                  // the stages hold the compact table
     size_t dyn = 0;
 };
 
@@ -217,19 +233,25 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     long long cap = budget > meta_bytes ? (budget - meta_bytes) / slot_bytes : 0;
     cap = std::min<long long>(cap, max_slots);
     cap &= ~3LL;
+    if (h->force_stream && mode == gfm::Mode::MIXED && max_slots > 0) cap = 0;
     if (meta_bytes > budget) return fail(h, GFM_ERR_ARG, "mesh too large for this launch shape");
     // Tables that do not fit: the mixed operator pass streams them through a
     // ring of 3 (else 2) stages, each a whole number of pass rounds (a round
     // = the slices the CTA's warps take at once: 4 per warp for rows of <= 6
     // faces, else 2).
     int n_stages = 0, stage_slices = 0, stage_cap = 0;
+    // the compact table streams 4 bytes per slot instead of 8, and stages
+    // its dictionary after the ring
+    const bool ct = mode == gfm::Mode::MIXED && h->ent_valid && h->ct_pref;
+    const long long sbytes = ct ? 4 : 8;
+    const long long dict_bytes = ct ? ((long long)(2 * h->n_cls + 1) * 4 + 15) / 16 * 16 : 0;
     if (mode == gfm::Mode::MIXED && cap < max_slots) {
         const int maxw = std::max(1, h->ht.max_width);
         const int unit = (maxw <= 6 ? 4 : 2) * (t / 32);
-        const long long per_unit = (long long)unit * 32 * maxw * 8;
+        const long long per_unit = (long long)unit * 32 * maxw * sbytes;
         const long long need = (max_nsl + unit - 1) / unit;
         for (int S = 3; S >= 2 && n_stages == 0; --S) {
-            const long long m = std::min<long long>((budget - meta_bytes) / (S * per_unit), need);
+            const long long m = std::min<long long>((budget - meta_bytes - dict_bytes) / (S * per_unit), need);
             if (m >= 1) {
                 n_stages = S;
                 stage_slices = (int)(unit * m);
@@ -238,10 +260,11 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
         }
         if (n_stages) cap = 0;
     }
-    const size_t dyn =
-        (size_t)(red_bytes + meta_bytes + (n_stages ? (long long)n_stages * stage_cap * 8 : cap * slot_bytes));
+    const size_t dyn = (size_t)(red_bytes + meta_bytes +
+                                (n_stages ? (long long)n_stages * stage_cap * sbytes + dict_bytes : cap * slot_bytes));
     if (n_stages)
-        k = h->batched ? gfm::batched_kernel(h->ht.max_width, true) : gfm::solver_kernel(mode, h->ht.max_width, t, true);
+        k = h->batched ? gfm::batched_kernel(h->ht.max_width, true, ct)
+                       : gfm::solver_kernel(mode, h->ht.max_width, t, true, ct);
     GFM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int occ = 0;
     GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, t, dyn));
@@ -253,6 +276,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     lp->n_stages = n_stages;
     lp->stage_slices = stage_slices;
     lp->stage_cap = stage_cap;
+    lp->ct = ct && n_stages > 0;
     lp->dyn = dyn;
     return GFM_OK;
 }
@@ -330,7 +354,7 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
     a.partials = h->partials;
     a.info = info_dev;
     gfm::BatchArgs ba{};
-    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads, lp.n_stages > 0);
+    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads, lp.n_stages > 0, lp.ct);
     if (h->batched) {
         a.n_per_tank = h->tncell;
         a.prm = h->tprm;
@@ -340,7 +364,7 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
         ba.tprm = h->tprm;
         ba.infos = info_dev;
         ba.tco = h->tco;
-        kernel = gfm::batched_kernel(h->ht.max_width, lp.n_stages > 0);
+        kernel = gfm::batched_kernel(h->ht.max_width, lp.n_stages > 0, lp.ct);
         GFM_CUDA(h, cudaMemsetAsync(info_dev, 0, sizeof(gfm_solve_info) * h->T, s));
     }
     void *args[] = {&a, &ba};
@@ -466,6 +490,74 @@ gfm_status alloc_upload(gfm_ctx *h, cudaStream_t s)
         if (e == cudaSuccess) e = cudaMemsetAsync(zp, 0, sizeof(float) * np, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "uploading tables");
+    return GFM_OK;
+}
+
+// Compact operator table (after the mesh is on the device).  Usable when
+// every slot's neighbour lies within a signed 16-bit offset of its own cell
+// and the faces fall into few classes of bit-identical c_f = S.S/S.d (per
+// tank in a batch): off the interface a face's FP32 coefficient is then one
+// of two dictionary values of its class, and each slot fits one word.  Not
+// usable: the full table streams, nothing else changes.
+gfm_status setup_compact(gfm_ctx *h, cudaStream_t s)
+{
+    h->ct_ok = false;
+    const gfm::HostTables &ht = h->ht;
+    for (int sl = 0; sl < ht.n_slices; ++sl) {
+        const int base = ht.slice_ptr[(size_t)sl], w = (ht.slice_ptr[(size_t)sl + 1] - base) / gfm::kSlice;
+        for (int k = 0; k < w; ++k)
+            for (int l = 0; l < gfm::kSlice; ++l) {
+                const size_t slot = (size_t)base + (size_t)k * gfm::kSlice + l;
+                if (ht.face[slot] == 0) continue;
+                const long long off = (long long)ht.col[slot] - ((long long)sl * gfm::kSlice + l);
+                if (off < -32768 || off > 32767) return GFM_OK;
+            }
+    }
+    const int F = h->F;
+    double *dc = nullptr;
+    if (dalloc(&dc, (size_t)F) != cudaSuccess) return fail(h, GFM_ERR_NOMEM, "compact table set-up");
+    std::vector<double> c((size_t)F);
+    cudaError_t e = gfm::launch_face_c(h->n, F, h->owner, h->neighbour, h->Sf, h->C, dc, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.data(), dc, sizeof(double) * F, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "compact table set-up");
+    const int max_cls = (gfm::kMaxDict - 1) / 2;
+    std::vector<int32_t> fcls((size_t)F), ctank;
+    std::vector<double> ccls;
+    std::unordered_map<unsigned long long, int32_t> seen;
+    int tank = -1;
+    for (int f = 0; f < F; ++f) {
+        const int t = h->batched ? h->bt.face_tank[(size_t)f] : 0;
+        if (t != tank) {  // faces are grouped by tank: classes never span tanks
+            seen.clear();
+            tank = t;
+        }
+        unsigned long long bits;
+        std::memcpy(&bits, &c[(size_t)f], sizeof(bits));
+        auto it = seen.find(bits);
+        if (it == seen.end()) {
+            if ((int)ccls.size() >= max_cls) return GFM_OK;
+            it = seen.emplace(bits, (int32_t)ccls.size()).first;
+            ccls.push_back(c[(size_t)f]);
+            ctank.push_back(t);
+        }
+        fcls[(size_t)f] = it->second;
+    }
+    const int ncls = (int)ccls.size();
+    e = dalloc(&h->ent, (size_t)ht.n_slots);
+    if (e == cudaSuccess) e = dalloc(&h->fcls, (size_t)F);
+    if (e == cudaSuccess) e = dalloc(&h->ccls, (size_t)ncls);
+    if (e == cudaSuccess) e = dalloc(&h->ctank, (size_t)ncls);
+    if (e == cudaSuccess) e = dalloc(&h->dict, (size_t)(2 * ncls + 1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->fcls, fcls.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ccls, ccls.data(), sizeof(double) * ncls, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctank, ctank.data(), sizeof(int32_t) * ncls, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return fail(h, e == cudaErrorMemoryAllocation ? GFM_ERR_NOMEM : GFM_ERR_CUDA, "compact table set-up");
+    h->n_cls = ncls;
+    h->ct_ok = true;
     return GFM_OK;
 }
 
@@ -602,7 +694,11 @@ gfm_status gfm_create(const gfm_mesh *mesh, int32_t renumber, gfm_stream stream,
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->Sf, mesh->Sf, sizeof(double) * 3 * F, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->C, mesh->C, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(h, e, "copying the mesh");
+        if (e != cudaSuccess) {
+            st = cuda_fail(h, e, "copying the mesh");
+            break;
+        }
+        st = setup_compact(h, s);
     } while (0);
     if (st != GFM_OK) {
         fprintf(stderr, "gfm_create: %s\n", h->last_error.c_str());
@@ -708,6 +804,8 @@ gfm_status gfm_create_batched(const gfm_mesh *meshes, int32_t n_tanks, int32_t r
             st = cuda_fail(h, e, "copying the tank meshes");
             break;
         }
+        st = setup_compact(h, s);
+        if (st != GFM_OK) break;
         st = plan_batch(h);
     } while (0);
     if (st != GFM_OK) {
@@ -792,7 +890,23 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     fa.rau = h->rau_set ? h->rau : nullptr;
     GFM_CUDA(h, gfm::launch_faces(fa, s));
     h->nonorth_active = false;
-    gfm::CellArgs ca;
+    // the compact table's codes hold only while gamma_f off the interface is
+    // c_f / rho of the phase, i.e. without a face Rhie-Chow coefficient
+    const bool use_ct = h->ct_ok && !h->rau_set;
+    int launched = 2;
+    if (use_ct) {
+        gfm::DictArgs da{};
+        da.n_cls = h->n_cls;
+        da.ccls = h->ccls;
+        da.ctank = h->batched ? h->ctank : nullptr;
+        da.tphys = h->batched ? h->tphys : nullptr;
+        da.rho_w = phys->rho_w;
+        da.rho_a = phys->rho_a;
+        da.dict = h->dict;
+        GFM_CUDA(h, gfm::launch_dict(da, s));
+        ++launched;
+    }
+    gfm::CellArgs ca{};
     ca.m = sell_of(h);
     ca.gamma = h->gamma;
     ca.sigma = h->sigma;
@@ -807,8 +921,12 @@ gfm_status gfm_assemble(gfm_handle h, const double *alpha, const double *phi, co
     ca.stank = h->batched ? h->stank : nullptr;
     ca.tphys = h->batched ? h->tphys : nullptr;
     ca.tprm = h->batched ? h->tprm : nullptr;
+    ca.ent = use_ct ? h->ent : nullptr;
+    ca.fcls = h->fcls;
+    ca.kind = h->kind;
+    ca.pad_code = 2 * h->n_cls;
     GFM_CUDA(h, gfm::launch_cells(ca, s));
-    int launched = 2;
+    h->ent_valid = use_ct;
     {
         gfm::CoarseArgs co{};
         co.n = h->n;
@@ -1090,8 +1208,8 @@ gfm_status gfm_nonorth_correct(gfm_handle h, const double *p, const double *V, c
     na.sigma = h->sigma;
     GFM_CUDA(h, gfm::launch_nonorth(na, s));
     // the cell sums again: b from the corrected sigma (diag and the tables
-    // are rewritten with the same values)
-    gfm::CellArgs ca;
+    // are rewritten with the same values; the compact table is unchanged)
+    gfm::CellArgs ca{};
     ca.m = sell_of(h);
     ca.gamma = h->gamma;
     ca.sigma = h->sigma;
@@ -1116,6 +1234,129 @@ gfm_status gfm_nonorth_correct(gfm_handle h, const double *p, const double *V, c
     h->nonorth_active = true;
     h->prof.launches = launched;
     h->prof.launches_total += launched;
+    return GFM_OK;
+}
+
+gfm_status gfm_piso_step(gfm_handle h, const gfm_solve_opts *opts, int32_t n_solves, int32_t n_nonorth,
+                         const double *alpha, const double *phi_star, const gfm_phys *phys, double *p, double *phi_corr,
+                         const double *V, const double *xf, double *grad, double *U, gfm_solve_info *info,
+                         gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    if (!opts || !alpha || !phi_star || !phys || !p || !info) return fail(h, GFM_ERR_ARG, "NULL argument");
+    if (!opts->info_on_device) return fail(h, GFM_ERR_ARG, "gfm_piso_step reports info on the device");
+    if (n_solves < 1 || n_nonorth < 0) return fail(h, GFM_ERR_ARG, "n_solves >= 1, n_nonorth >= 0");
+    if ((n_nonorth > 0 || grad || U) && !V) return fail(h, GFM_ERR_ARG, "the gradient steps need V");
+    const bool batched = h->batched;
+    cudaStream_t s = (cudaStream_t)stream;
+    gfm_solve_opts o = *opts;
+    for (int k = 0; k < n_solves; ++k) {
+        // corrector k: the pressure equation of its predicted flux, solved
+        // from the last corrector's p_d (the first from opts->use_x0).  alpha
+        // is the step's, so after the first full assembly only the source
+        // changes: sigma and the cell sums again, bit-identical to a full
+        // assembly with this flux
+        gfm_status st = GFM_OK;
+        if (k == 0) {
+            st = gfm_assemble(h, alpha, phi_star, phys, stream);
+            if (st != GFM_OK) return st;
+        } else {
+            const double *phik = phi_star + (size_t)k * h->F;
+            GFM_CUDA(h, cudaMemcpyAsync(h->phi, phik, sizeof(double) * h->F, cudaMemcpyDeviceToDevice, s));
+            GFM_CUDA(h, gfm::launch_sigma(h->F, h->phi, h->gamma, h->jump, h->sigma, s));
+            gfm::CellArgs ca{};
+            ca.m = sell_of(h);
+            ca.gamma = h->gamma;
+            ca.sigma = h->sigma;
+            ca.ref = h->ref_internal;
+            ca.ref_value = h->phys.ref_value;
+            ca.b = h->b;
+            ca.diag = h->diag;
+            ca.dinv = h->dinv;
+            ca.dinv32 = h->dinv32;
+            ca.prm = h->prm;
+            ca.iperm = h->iperm;
+            ca.stank = batched ? h->stank : nullptr;
+            ca.tphys = batched ? h->tphys : nullptr;
+            ca.tprm = batched ? h->tprm : nullptr;
+            GFM_CUDA(h, gfm::launch_cells(ca, s));
+            if (h->ref_internal < 0) GFM_CUDA(h, gfm::launch_bsums(h->b, h->n, h->prm, s));
+            h->nonorth_active = false;
+        }
+        o.use_x0 = (k == 0) ? opts->use_x0 : 1;
+        const bool last = k == n_solves - 1;
+        gfm_solve_info *ik = info + (size_t)k * (batched ? h->T : 1);
+        st = gfm_solve(h, &o, p, (last && n_nonorth == 0) ? phi_corr : nullptr, ik, stream);
+        if (st != GFM_OK) return st;
+        for (int j = 0; j < n_nonorth; ++j) {
+            st = gfm_nonorth_correct(h, p, V, xf, nullptr, stream);
+            if (st != GFM_OK) return st;
+            o.use_x0 = 1;
+            st = gfm_solve(h, &o, p, (last && j == n_nonorth - 1) ? phi_corr : nullptr, ik, stream);
+            if (st != GFM_OK) return st;
+        }
+    }
+    if (grad || U) {
+        if (U && !phi_corr) return fail(h, GFM_ERR_ARG, "U needs phi_corr");
+        return gfm_gradient(h, p, V, xf, grad, phi_corr, U, stream);
+    }
+    return GFM_OK;
+}
+
+gfm_status gfm_iso_advect(gfm_handle h, const double *alpha, const double *phi, double dt, const int32_t *fv_ptr,
+                          const double *fv_xyz, int32_t nvt, const double *xf, const int8_t *has_iso,
+                          const double *xS, const double *nS, const double *UnS, const double *V, double *integral,
+                          double *dV, double *alpha_new, gfm_stream stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    if (!alpha || !phi || !fv_ptr || !fv_xyz || !xf || !has_iso || !xS || !nS || !UnS || !dV)
+        return fail(h, GFM_ERR_ARG, "NULL argument");
+    if (alpha_new && !V) return fail(h, GFM_ERR_ARG, "the alpha update needs V");
+    if (!(dt >= 0.0) || !std::isfinite(dt) || nvt < 3) return fail(h, GFM_ERR_ARG, "dt >= 0 and nvt >= 3");
+    clear_stale_error();
+    gfm::IsoArgs a{};
+    a.m = sell_of(h);
+    a.n = h->n;
+    a.F = h->F;
+    a.nvt = nvt;
+    a.iperm = h->iperm;
+    a.owner = h->owner;
+    a.neighbour = h->neighbour;
+    a.alpha = alpha;
+    a.phi = phi;
+    a.dt = dt;
+    a.fv_ptr = fv_ptr;
+    a.fv_xyz = fv_xyz;
+    a.xf = xf;
+    a.has_iso = has_iso;
+    a.xS = xS;
+    a.nS = nS;
+    a.UnS = UnS;
+    a.V = V;
+    a.integral = integral;
+    a.dV = dV;
+    a.alpha_new = alpha_new;
+    GFM_CUDA(h, gfm::launch_iso(a, (cudaStream_t)stream));
+    const int launched = alpha_new ? 2 : 1;
+    h->prof.launches = launched;
+    h->prof.launches_total += launched;
+    return GFM_OK;
+}
+
+gfm_status gfm_set_table(gfm_handle h, int32_t compact, int32_t force_stream)
+{
+    if (!h) return GFM_ERR_ARG;
+    h->ct_pref = compact != 0;
+    h->force_stream = force_stream != 0;
+    return GFM_OK;
+}
+
+gfm_status gfm_get_table(gfm_handle h, int32_t *compact_usable, int32_t *n_classes, int32_t *compact_valid)
+{
+    if (!h) return GFM_ERR_ARG;
+    if (compact_usable) *compact_usable = h->ct_ok ? 1 : 0;
+    if (n_classes) *n_classes = h->n_cls;
+    if (compact_valid) *compact_valid = h->ent_valid ? 1 : 0;
     return GFM_OK;
 }
 

@@ -107,6 +107,7 @@ __global__ void k_cells(CellArgs a)
         if (code == 0) {
             a.m.val64[slot] = 0.0;
             a.m.val32[slot] = 0.0f;
+            if (a.ent) a.ent[slot] = (uint32_t)a.pad_code << 16;  // itself, coefficient 0
             continue;
         }
         const int f = (code > 0 ? code : -code) - 1;
@@ -116,6 +117,15 @@ __global__ void k_cells(CellArgs a)
         b = (code > 0) ? b - sg : b + sg;
         a.m.val64[slot] = g;
         a.m.val32[slot] = (float)g;
+        if (a.ent) {
+            // off the interface the coefficient is the class's one for the
+            // face's phase; interface faces read val32 (escape)
+            const int8_t kd = a.kind[f];
+            const uint32_t vc = kd == kWet ? (uint32_t)(2 * a.fcls[f]) : kd == kDry ? (uint32_t)(2 * a.fcls[f] + 1)
+                                                                                  : kEscape;
+            const int off = a.m.col[slot] - t;
+            a.ent[slot] = (vc << 16) | ((uint32_t)off & 0xFFFFu);
+        }
     }
     if (t == ref) {
         b = b + diag * ref_value;
@@ -127,6 +137,55 @@ __global__ void k_cells(CellArgs a)
     a.diag[t] = valid ? diag : 0.0;
     a.dinv[t] = valid ? 1.0 / diag : 0.0;
     a.dinv32[t] = valid ? 1.0f / (float)diag : 0.0f;
+}
+
+// sigma = phi + gamma J for a new predicted flux on an assembled system (the
+// interface, the coefficients and the jump unchanged), rounded as in k_faces.
+__global__ void k_sigma(int F, const double *__restrict__ phi, const double *__restrict__ gamma,
+                        const double *__restrict__ jump, double *__restrict__ sigma)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    sigma[f] = phi[f] + gamma[f] * jump[f];
+}
+
+// c_f = (S.S)/(S.d) per face, the geometric factor of gamma_f, rounded as in
+// k_faces (the compact table groups faces of bit-identical c_f into classes).
+__global__ void k_face_c(int n, int F, const int32_t *__restrict__ owner, const int32_t *__restrict__ neighbour,
+                         const double *__restrict__ Sf, const double *__restrict__ C, double *__restrict__ out)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const int o = owner[f], nb = neighbour[f];
+    const size_t nn = (size_t)n, FF = (size_t)F;
+    const double Sx = Sf[f], Sy = Sf[FF + f], Sz = Sf[2 * FF + f];
+    const double dx = C[nb] - C[o];
+    const double dy = C[nn + nb] - C[nn + o];
+    const double dz = C[2 * nn + nb] - C[2 * nn + o];
+    out[f] = (Sx * Sx + Sy * Sy + Sz * Sz) / (Sx * dx + Sy * dy + Sz * dz);
+}
+
+// Dictionary of the compact table: the off-interface coefficients
+// c / (lambda rho_w + (1 - lambda) rho_a) with lambda = 1 (wet) and 0 (dry),
+// written with k_faces' expression so each entry has the bits of the
+// gamma_f (as FP32) of the faces it stands for.
+__global__ void k_dict(DictArgs a)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) a.dict[2 * a.n_cls] = 0.0f;  // padding slots
+    if (k >= a.n_cls) return;
+    double rho_w = a.rho_w, rho_a = a.rho_a;
+    if (a.ctank) {
+        const TankPhys tp = a.tphys[a.ctank[k]];
+        rho_w = tp.rho_w;
+        rho_a = tp.rho_a;
+    }
+    const double c = a.ccls[k];
+    const double lw = 1.0, ld = 0.0;
+    const double rfw = lw * rho_w + (1.0 - lw) * rho_a;
+    const double rfd = ld * rho_w + (1.0 - ld) * rho_a;
+    a.dict[2 * k] = (float)(c / rfw);
+    a.dict[2 * k + 1] = (float)(c / rfd);
 }
 
 // sum(b) and sum(|b|) by one block, fixed order (compatibility check of an
@@ -259,6 +318,28 @@ cudaError_t launch_cells(const CellArgs &a, cudaStream_t s)
 cudaError_t launch_bsums(const double *b, int32_t n, DevParams *prm, cudaStream_t s)
 {
     k_bsums<<<1, 1024, 0, s>>>(b, n, prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_c(int32_t n, int32_t F, const int32_t *owner, const int32_t *neighbour, const double *Sf,
+                          const double *C, double *c, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    k_face_c<<<blocks_for(F, 256), 256, 0, s>>>(n, F, owner, neighbour, Sf, C, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma(int32_t F, const double *phi, const double *gamma, const double *jump, double *sigma,
+                         cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    k_sigma<<<blocks_for(F, 256), 256, 0, s>>>(F, phi, gamma, jump, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dict(const DictArgs &a, cudaStream_t s)
+{
+    k_dict<<<blocks_for(a.n_cls + 1, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -89,7 +89,16 @@ struct Sell {
     const int32_t *face;       // [n_slots] +(f+1) if the cell owns face f, -(f+1) if neighbour, 0 pad
     double *val64;             // [n_slots] gamma_f   (FP64)
     float *val32;              // [n_slots] (float)gamma_f
+    // Compact form of the same table for the streamed mixed operator pass
+    // (nullptr when unused): per slot (value code << 16) | (uint16)(col - i),
+    // i the slot's own cell; a code indexes dict, kEscape means "read val32".
+    const uint32_t *ent;       // [n_slots]
+    const float *dict;         // [n_dict] FP32 coefficients; the last one is 0 (padding)
+    int32_t n_dict;
 };
+
+constexpr uint32_t kEscape = 0xFFFFu;  // compact-table code: coefficient not in the dictionary
+constexpr int kMaxDict = 4096;         // dictionary entries (FP32), staged in shared memory
 
 // Everything a persistent solver kernel needs.  Vectors are in internal order
 // and padded to n_pad.
@@ -154,8 +163,36 @@ struct CellArgs {
     const int32_t *stank;    // batched: tank of each slice (else nullptr)
     const TankPhys *tphys;   // batched: ref cell and value per tank
     DevParams *tprm;         // batched: pin per tank
+    // compact table (nullptr = not written): codes from the face's kind and
+    // geometric class (2 cls for a wet face, 2 cls + 1 for a dry one)
+    uint32_t *ent;
+    const int32_t *fcls;
+    const int8_t *kind;
+    int32_t pad_code;
 };
 cudaError_t launch_cells(const CellArgs &a, cudaStream_t s);
+
+// sigma = phi + gamma J for a new predicted flux (coefficients unchanged)
+cudaError_t launch_sigma(int32_t F, const double *phi, const double *gamma, const double *jump, double *sigma,
+                         cudaStream_t s);
+
+// c_f = (S.S)/(S.d) of every face, rounded exactly as the face assembly does
+cudaError_t launch_face_c(int32_t n, int32_t F, const int32_t *owner, const int32_t *neighbour, const double *Sf,
+                          const double *C, double *c, cudaStream_t s);
+
+// Dictionary of the compact table: dict[2k] = (float)(c_k / rho_w),
+// dict[2k+1] = (float)(c_k / rho_a) for geometric class k (densities of the
+// class's tank when batched), dict[2 n_cls] = 0, each rounded exactly as the
+// face assembly rounds gamma_f off the interface.
+struct DictArgs {
+    int32_t n_cls;
+    const double *ccls;
+    const int32_t *ctank;    // batched: tank of each class (else nullptr)
+    const TankPhys *tphys;
+    double rho_w, rho_a;
+    float *dict;
+};
+cudaError_t launch_dict(const DictArgs &a, cudaStream_t s);
 cudaError_t launch_bsums(const double *b, int32_t n, DevParams *prm, cudaStream_t s);
 
 struct CoarseArgs {
@@ -232,6 +269,26 @@ struct NonorthArgs {
 };
 cudaError_t launch_nonorth(const NonorthArgs &a, cudaStream_t s);
 
+// ---- isoAdvector advection step (gfm_iso.cu) ------------------------------
+struct IsoArgs {
+    Sell m;
+    int32_t n, F, nvt;
+    const int32_t *iperm, *owner, *neighbour;
+    const double *alpha, *phi;
+    double dt;
+    const int32_t *fv_ptr;   // [F+1]
+    const double *fv_xyz;    // [3][nvt]
+    const double *xf;        // [3][F] triangle apexes
+    const int8_t *has_iso;   // [n]
+    const double *xS, *nS;   // [3][n]
+    const double *UnS;       // [n]
+    const double *V;         // [n]
+    double *integral;        // [F] nullable
+    double *dV;              // [F]
+    double *alpha_new;       // [n] nullable
+};
+cudaError_t launch_iso(const IsoArgs &a, cudaStream_t s);
+
 cudaError_t launch_gather(const double *src_user, const int32_t *iperm, double *dst_internal, int32_t n,
                           int32_t n_pad, cudaStream_t s);
 
@@ -247,10 +304,10 @@ struct BatchArgs {
     gfm_solve_info *infos;  // [T]
     const TankCoarse *tco;  // [T] coarse space of each tank
 };
-const void *batched_kernel(int max_width, bool streamed = false);
+const void *batched_kernel(int max_width, bool streamed = false, bool compact = false);
 
 enum class Mode { FP64 = 0, MIXED = 1 };
-const void *solver_kernel(Mode m, int max_width, int threads, bool streamed = false);
+const void *solver_kernel(Mode m, int max_width, int threads, bool streamed = false, bool compact = false);
 int solver_max_threads();
 
 }  // namespace gfm

@@ -77,6 +77,7 @@ constexpr int kMaxNR = 12;
 // Values decided by thread 0 and broadcast to the CTA.
 struct Ctl {
     double alpha, beta, xavg;
+    float gam32;  // MIXED: (float) r.u of the last iteration, for alpha
     float al, be;
     int action;
 };
@@ -97,6 +98,7 @@ struct Shared {
     float zpin32;  // the pinned cell's share, when this CTA holds it
     double zpin64;
     double Einv[kMaxCoarse * kMaxCoarse];  // staged copy of the coarse inverse
+    float Einv32[kMaxCoarse * kMaxCoarse];  // the same in FP32 (the FP32 iterations' coarse correction)
     int flag;
     int flag2;  // a reduction's error check, published with its sums
     int ring_fail;  // a streamed-table stage did not arrive within the budget
@@ -333,7 +335,7 @@ struct Tab {
         const int2 m = meta[s - s0];
         return Row{m.x, m.y};
     }
-    __device__ __forceinline__ int c(int slot) const { return slot < end ? col[slot - base0] : __ldg(gcol + slot); }
+    __device__ __forceinline__ int c(int slot, int) const { return slot < end ? col[slot - base0] : __ldg(gcol + slot); }
     __device__ __forceinline__ V v(int slot) const { return slot < end ? val[slot - base0] : __ldg(gval + slot); }
 };
 
@@ -425,12 +427,15 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 }
 
 struct Ring {
-    unsigned char *buf;       // n_stages x (col [cap] | val [cap])
+    unsigned char *buf;       // n_stages x (col [cap] | val [cap]), or n_stages x ent [cap] (compact)
     unsigned long long *bar;  // [n_stages]
     const int2 *meta;         // the CTA's staged slice (base, width)
     const int32_t *gcol;
     const float *gval;
+    const uint32_t *gent;     // compact table (ct), else unused
+    const float *dict;        // compact table: the coefficient dictionary, staged after the stages
     int n_stages, stage_slices, cap, nsl, nr, s0, tab_end;
+    int ct;                   // 1: the stages hold the compact table (4 bytes per slot)
     unsigned issued;  // stages requested so far (thread 0 only)
     unsigned used;    // stages consumed so far (every thread)
 };
@@ -450,6 +455,13 @@ __device__ __forceinline__ void ring_issue(Ring &g, int r)
     unsigned long long *bar = g.bar + st;
     const int b = ring_begin(g, r);
     const unsigned bytes = (unsigned)(ring_end(g, r) - b) * 4u;
+    if (g.ct) {
+        uint32_t *ent = reinterpret_cast<uint32_t *>(g.buf + (size_t)st * g.cap * 4);
+        mbar_arrive_expect_tx(bar, bytes);
+        if (bytes != 0u) bulk_load(ent, g.gent + b, bytes, bar, l2_evict_first());
+        ++g.issued;
+        return;
+    }
     int32_t *col = reinterpret_cast<int32_t *>(g.buf + (size_t)st * g.cap * 8);
     float *val = reinterpret_cast<float *>(col + g.cap);
     mbar_arrive_expect_tx(bar, 2u * bytes);
@@ -501,7 +513,7 @@ struct StageTab {
         const int2 m = meta[s - s0];
         return Row{m.x, m.y};
     }
-    __device__ __forceinline__ int c(int slot) const { return col[slot - begin]; }
+    __device__ __forceinline__ int c(int slot, int) const { return col[slot - begin]; }
     __device__ __forceinline__ float v(int slot) const { return val[slot - begin]; }
 };
 
@@ -512,9 +524,49 @@ __device__ __forceinline__ StageTab ring_stage(const Ring &g, int r)
     return StageTab{g.meta, col, reinterpret_cast<const float *>(col + g.cap), g.s0, ring_begin(g, r)};
 }
 
+// Table view of a compact stage: per slot one word, the neighbour as a
+// signed 16-bit offset from the slot's own cell and a 16-bit code of its
+// coefficient -- an entry of the dictionary (the few off-interface values
+// of each geometric class of faces, staged in shared memory) or, for an
+// interface face, kEscape: its coefficient is read from the FP32 table in
+// global memory, a load issued beside the neighbour gather.  Half the bytes
+// of (index, coefficient) per slot.
+struct StageTabCT {
+    const int2 *meta;
+    const uint32_t *ent;
+    const float *dict;
+    const float *gval;
+    int s0, begin;
+
+    __device__ __forceinline__ Row row(int s) const
+    {
+        const int2 m = meta[s - s0];
+        return Row{m.x, m.y};
+    }
+    __device__ __forceinline__ int c(int slot, int i) const
+    {
+        return i + (int)(int16_t)(ent[slot - begin] & 0xFFFFu);
+    }
+    __device__ __forceinline__ float v(int slot) const
+    {
+        const uint32_t code = ent[slot - begin] >> 16;
+        return code != kEscape ? dict[code] : __ldg(gval + slot);
+    }
+};
+
+__device__ __forceinline__ StageTabCT ring_stage_ct(const Ring &g, int r)
+{
+    const int st = (int)(g.used % (unsigned)g.n_stages);
+    const uint32_t *ent = reinterpret_cast<const uint32_t *>(g.buf + (size_t)st * g.cap * 4);
+    return StageTabCT{g.meta, ent, g.dict, g.gval, g.s0, ring_begin(g, r)};
+}
+
 // Set up the ring after stage_tables (the slice metadata is in shared
-// memory).  n_stages = 0: tables are read from the static cache / L2.
-__device__ Ring make_ring(const SolveArgs &a, const Range &R, const int2 *meta, unsigned char *dsm, Shared &sh)
+// memory).  n_stages = 0: tables are read from the static cache / L2.  With
+// `ct` the stages hold the compact table and the dictionary is staged after
+// them for the whole solve.
+__device__ Ring make_ring(const SolveArgs &a, const Range &R, const int2 *meta, unsigned char *dsm, Shared &sh,
+                          bool ct = false)
 {
     Ring g{};
     g.n_stages = a.n_stages;
@@ -524,6 +576,13 @@ __device__ Ring make_ring(const SolveArgs &a, const Range &R, const int2 *meta, 
     g.meta = meta;
     g.gcol = a.m.col;
     g.gval = a.m.val32;
+    g.gent = a.m.ent;
+    g.ct = ct ? 1 : 0;
+    if (ct) {
+        float *d = reinterpret_cast<float *>(g.buf + (size_t)a.n_stages * a.stage_cap * 4);
+        for (int k = threadIdx.x; k < a.m.n_dict; k += blockDim.x) d[k] = __ldg(a.m.dict + k);
+        g.dict = d;
+    }
     g.stage_slices = a.stage_slices;
     g.cap = a.stage_cap;
     g.s0 = R.s0;
@@ -691,7 +750,27 @@ __device__ __forceinline__ void coarse_solve_warp(int K, Shared &sh)
 // Copy E^{-1} into shared memory once per solve.
 __device__ __forceinline__ void stage_coarse(const Coarse *co, Shared &sh)
 {
-    for (int q = threadIdx.x; q < kMaxCoarse * kMaxCoarse; q += blockDim.x) sh.Einv[q] = co->Einv[q];
+    for (int q = threadIdx.x; q < kMaxCoarse * kMaxCoarse; q += blockDim.x) {
+        sh.Einv[q] = co->Einv[q];
+        sh.Einv32[q] = (float)co->Einv[q];
+    }
+}
+
+// One warp, all lanes: lane k < K returns c_k = sum_j E^{-1}_kj y_j in FP32,
+// y_j taken from lane j's y (lanes >= K return 0).  The FP32 iterations only
+// need the correction in FP32, and on GB300 a chain of K dependent FP64
+// multiply-adds costs several times this shuffle-and-FMA form.
+__device__ __forceinline__ float coarse32_lane(int K, double y_lane, const Shared &sh)
+{
+    const int k = threadIdx.x & 31;
+    const float yl = (float)y_lane;
+    float c = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kMaxCoarse; ++j) {
+        const float yj = __shfl_sync(0xffffffffu, yl, j);
+        if (j < K && k < K) c = fmaf(sh.Einv32[k * kMaxCoarse + j], yj, c);
+    }
+    return c;
 }
 
 __device__ __forceinline__ void zero_bins(Shared &sh)
@@ -908,7 +987,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_fp64(SolveArgs a)
                     for (int c = 0; c < CH; ++c) {
                         const bool ok = k0 + c < w[u];
                         const int slot = base[u] + (k0 + c) * kSlice + R.lane;
-                        j[u][c] = ok ? tab.c(slot) : 0;
+                        j[u][c] = ok ? tab.c(slot, 0) : 0;
                         gm[u][c] = ok ? tab.v(slot) : 0.0;
                     }
 #pragma unroll
@@ -1124,7 +1203,7 @@ namespace {
 // t = (||r||^2 in FP64, r32.u, r32.r32) and sh.y = Z^T r32.
 template <int CH>
 __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, float2 *up, double sc,
-                                 double isc, bool fold, bool zero_p, double (&t)[3])
+                                 double isc, bool fold, bool zero_p, double (&t)[3], double &y_lane)
 {
     const int n = a.m.n;
     const int ref = a.prm->ref;
@@ -1172,7 +1251,12 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
     if (threadIdx.x < 32) {
         if (threadIdx.x == 0)
             for (int k = 0; k < K; ++k) sh.y[k] = tt[3 + k];
-        coarse_solve_warp(K, sh);
+        coarse_solve_warp(K, sh);  // c in FP64, for r.u below
+        // warp 0's register copy of y, and the FP32 correction the FP32
+        // iterations apply (the same form as in every iteration)
+        y_lane = (R.lane < K) ? tt[3 + R.lane] : 0.0;
+        const float c = coarse32_lane(K, y_lane, sh);
+        if (R.lane < K) sh.c32[R.lane] = c;
     }
     if (threadIdx.x == 0) {
         double gam = tt[1];
@@ -1180,6 +1264,7 @@ __device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const 
         t[0] = tt[0];
         t[1] = gam;
         t[2] = tt[2];
+        sh.ctl.gam32 = (float)gam;
     }
     __syncthreads();
     if (K > 0) {
@@ -1230,7 +1315,7 @@ __device__ __forceinline__ void mixed_op_group(const TabT &tab, int sb, int s_en
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const bool ok = k0 + c < w[u];
-                vj[u][c] = ok ? cur[tab.c(base[u] + (k0 + c) * kSlice + R.lane)] : v[u];
+                vj[u][c] = ok ? cur[tab.c(base[u] + (k0 + c) * kSlice + R.lane, ii[u])] : v[u];
             }
         if (k0 == 0) {
 #pragma unroll
@@ -1306,7 +1391,7 @@ __device__ __forceinline__ void mixed_op_group_hoisted(const TabT &tab, int sb, 
             for (int c = 0; c < CH; ++c) {
                 const bool ok = k0 + c < w[u];
                 const int slot = base[u] + (k0 + c) * kSlice + R.lane;
-                j[u][c] = ok ? tab.c(slot) : 0;
+                j[u][c] = ok ? tab.c(slot, ii[u]) : 0;
                 gm[u][c] = ok ? tab.v(slot) : 0.0f;
             }
 #pragma unroll
@@ -1331,7 +1416,7 @@ __device__ __forceinline__ void mixed_op_group_hoisted(const TabT &tab, int sb, 
 
 }  // namespace
 
-template <int CH, bool STREAM>
+template <int CH, bool STREAM, bool CT = false>
 __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 {
     // slices per warp in one operator group with cached tables: one for
@@ -1347,7 +1432,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     stage_coarse(a.coarse, sh);
     const Tab<float> tab = stage_tables<float>(a.m, a.m.val32, R, a.cache_cap, a.meta_slots, dsm);
     Ring ring{};
-    if constexpr (STREAM) ring = make_ring(a, R, tab.meta, dsm, sh);
+    if constexpr (STREAM) ring = make_ring(a, R, tab.meta, dsm, sh, CT);
     // every early return first lets the stages still in flight land
     auto bail = [&]() {
         if constexpr (STREAM)
@@ -1401,7 +1486,8 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     float2 *cur = a.UP0, *nxt = a.UP1;  // cur holds (u, p_old) for the next pass A
     int iters = 0, updates = 0, status = GFM_OK;
     double t[3];
-    if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, false, true, t)) { bail(); return; }
+    double y_lane = 0.0;  // warp 0: Z^T r (lane k: component k)
+    if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, false, true, t, y_lane)) { bail(); return; }
     ++updates;
     if (threadIdx.x == 0) {
         best_rel2 = t[0] / (bnorm * bnorm);
@@ -1425,9 +1511,17 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 if (ring_wait(ring, a.budget_ns)) {
                     const int sr0 = R.s0 + r * ring.stage_slices;
                     const int sr1 = min(R.s1, sr0 + ring.stage_slices);
-                    const StageTab st = ring_stage(ring, r);
-                    for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
-                        mixed_op_group<CH, US>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh, accA[0]);
+                    if constexpr (CT) {
+                        const StageTabCT st = ring_stage_ct(ring, r);
+                        for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                            mixed_op_group<CH, US>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh,
+                                                   accA[0]);
+                    } else {
+                        const StageTab st = ring_stage(ring, r);
+                        for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                            mixed_op_group<CH, US>(st, sb, sr1, R, n, cur, P32, S32, be, ref, pin32, rc, K, sh,
+                                                   accA[0]);
+                    }
                 } else {
                     sh.ring_fail = 1;
                 }
@@ -1472,27 +1566,32 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
             tA[0] = o1[0];
         }
         if (threadIdx.x < 32) {
-            // alpha in FP32 (the vectors use it in FP32; an FP64 divide by one
-            // thread costs far more), then lane k updates y_k and the warp
-            // forms the coarse correction
+            // warp 0: alpha in FP32 (the vectors use it in FP32), lane k
+            // updates y_k (FP64) and the warp forms the FP32 coarse
+            // correction; FP64 work stays in this one warp (GB300's FP64 pipe
+            // would serialise it across all warps of the SM)
+            const float ps32 = (float)tA[0], gam32 = sh.ctl.gam32;
+            const bool ok = ps32 > 0.0f && isfinite(ps32) && gam32 > 0.0f;
+            const float al0 = ok ? gam32 / ps32 : 0.0f;
             if (threadIdx.x == 0) {
-                const double ps = tA[0];
-                const bool ok = ps > 0.0 && isfinite(ps) && gam > 0.0;
-                sh.ctl.al = ok ? (float)gam / (float)ps : 0.0f;
+                sh.ctl.al = al0;
                 sh.ctl.action = ok ? kGo : kRestart;
             }
-            __syncwarp();
             double zk = 0.0;  // this lane's (Z^T A p)_k, picked without indexing the array at run time
 #pragma unroll
             for (int k = 0; k < kMaxCoarse; ++k)
-                if (k == (int)threadIdx.x) zk = tA[1 + k];
-            if ((int)threadIdx.x < K) sh.y[threadIdx.x] = fma(-(double)sh.ctl.al, zk, sh.y[threadIdx.x]);
-            coarse_solve_warp(K, sh);
+                if (k == R.lane) zk = tA[1 + k];
+            if (R.lane < K) {
+                y_lane = fma(-(double)al0, zk, y_lane);
+                sh.y[R.lane] = y_lane;
+            }
+            const float c = coarse32_lane(K, y_lane, sh);
+            if (R.lane < K) sh.c32[R.lane] = c;
         }
         __syncthreads();
         if (sh.ctl.action == kRestart) {
             // breakdown of the FP32 recurrence: restart from the true residual
-            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, true, t)) { bail(); return; }
+            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, true, t, y_lane)) { bail(); return; }
             ++updates;
             if (threadIdx.x == 0) {
                 const double rel2 = t[0] / (bnorm * bnorm);
@@ -1564,13 +1663,14 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 sh.ctl.be = (float)gam / (float)gam_prev;
                 sh.ctl.action = kGo;
             }
+            sh.ctl.gam32 = (float)gam;
         }
         __syncthreads();
         action = sh.ctl.action;
         if (action == kUpdate || action == kNotConverged) {
             // fold e into x (FP64) and replace r by the true residual; the
             // direction p is kept
-            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, false, t)) { bail(); return; }
+            if (!replace_residual<CH>(a, g, sh, R, cur, sc, isc, true, false, t, y_lane)) { bail(); return; }
             ++updates;
             if (threadIdx.x == 0) {
                 const double rel2 = t[0] / (bnorm * bnorm);
@@ -1586,6 +1686,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                         rho_max = t[2];
                         sh.ctl.be = (gam > 0.0 && gam_prev > 0.0) ? (float)(gam / gam_prev) : 0.0f;
                         sh.ctl.action = kGo;
+                        sh.ctl.gam32 = (float)gam;
                     }
                 }
             }
@@ -1895,7 +1996,7 @@ struct BTab {
         const int b = __ldg(gptr + s);
         return Row{b, (__ldg(gptr + s + 1) - b) >> 5};
     }
-    __device__ __forceinline__ int c(int slot) const { return slot < end ? col[slot - base0] : __ldg(gcol + slot); }
+    __device__ __forceinline__ int c(int slot, int) const { return slot < end ? col[slot - base0] : __ldg(gcol + slot); }
     __device__ __forceinline__ float v(int slot) const { return slot < end ? val[slot - base0] : __ldg(gval + slot); }
 };
 
@@ -1948,7 +2049,7 @@ __device__ void batch_abort(const SolveArgs &a, const BatchArgs &bt)
 
 }  // namespace
 
-template <int CH, bool STREAM>
+template <int CH, bool STREAM, bool CT = false>
 __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs bt)
 {
     constexpr int U = 16 / CH;           // slices in flight per warp in the operator pass
@@ -1994,7 +2095,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     // the metadata area (the host sizes it for every re-plan) is an error
     Ring ring{};
     if constexpr (STREAM) {
-        ring = make_ring(a, R, tab.meta, tdsm, sh);
+        ring = make_ring(a, R, tab.meta, tdsm, sh, CT);
         ring_retarget(ring, R.s0, tab.nmeta, tab.meta);
         if (threadIdx.x == 0 && tab.nmeta < R.s1 - R.s0) atomicCAS(a.err, 0, (int)GFM_ERR_STATE);
     }
@@ -2133,10 +2234,17 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                     if (work) {
                         const int sr0 = ring.s0 + r * ring.stage_slices;
                         const int sr1 = min(ring.s0 + ring.nsl, sr0 + ring.stage_slices);
-                        const StageTab st = ring_stage(ring, r);
-                        for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
-                            mixed_op_group<CH, US>(st, sb, sr1, R, cend, cur, P32, S32, be, ref, pin32, ts.rc[tank],
-                                                   Kt, sh, accA[0]);
+                        if constexpr (CT) {
+                            const StageTabCT st = ring_stage_ct(ring, r);
+                            for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                                mixed_op_group<CH, US>(st, sb, sr1, R, cend, cur, P32, S32, be, ref, pin32,
+                                                       ts.rc[tank], Kt, sh, accA[0]);
+                        } else {
+                            const StageTab st = ring_stage(ring, r);
+                            for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                                mixed_op_group<CH, US>(st, sb, sr1, R, cend, cur, P32, S32, be, ref, pin32,
+                                                       ts.rc[tank], Kt, sh, accA[0]);
+                        }
                     }
                 } else {
                     sh.ring_fail = 1;
@@ -2412,24 +2520,35 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     }
 }
 
-const void *batched_kernel(int max_width, bool streamed)
+const void *batched_kernel(int max_width, bool streamed, bool compact)
 {
-    if (max_width <= 4) return streamed ? (const void *)k_solve_batched<4, true> : (const void *)k_solve_batched<4, false>;
+    if (max_width <= 4) {
+        if (streamed && compact) return (const void *)k_solve_batched<4, true, true>;
+        return streamed ? (const void *)k_solve_batched<4, true> : (const void *)k_solve_batched<4, false>;
+    }
+    if (streamed && compact) return (const void *)k_solve_batched<8, true, true>;
     return streamed ? (const void *)k_solve_batched<8, true> : (const void *)k_solve_batched<8, false>;
 }
 
 // Instantiations by faces per row chunk (4 for 2D hex meshes, 8 otherwise)
 // and, for the mixed solver, by how the operator pass reads the tables
-// (streamed through shared-memory stages, or cached / read in place).
-const void *solver_kernel(Mode m, int max_width, int threads, bool streamed)
+// (streamed through shared-memory stages -- in full or compact form -- or
+// cached / read in place).
+const void *solver_kernel(Mode m, int max_width, int threads, bool streamed, bool compact)
 {
     (void)threads;
+    const bool ct = streamed && compact;
     if (max_width <= 4) {
         if (m == Mode::FP64) return (const void *)k_solve_fp64<4>;
+        if (ct) return (const void *)k_solve_mixed<4, true, true>;
         return streamed ? (const void *)k_solve_mixed<4, true> : (const void *)k_solve_mixed<4, false>;
     }
     if (m == Mode::FP64) return (const void *)k_solve_fp64<8>;
-    if (streamed && max_width <= 6) return (const void *)k_solve_mixed<6, true>;  // hexahedra
+    if (streamed && max_width <= 6) {  // hexahedra
+        if (ct) return (const void *)k_solve_mixed<6, true, true>;
+        return (const void *)k_solve_mixed<6, true>;
+    }
+    if (ct) return (const void *)k_solve_mixed<8, true, true>;
     return streamed ? (const void *)k_solve_mixed<8, true> : (const void *)k_solve_mixed<8, false>;
 }
 
