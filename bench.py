@@ -550,6 +550,114 @@ class Batch64:
                 "api": "GFMBatch.assemble/solve (pinned host buffers, copies in the timed region)"}
 
 
+def piso_fluxes(case, n_solves: int, seed: int = 77):
+    """Predicted fluxes of the n_solves pressure correctors of one time step:
+    the case's flux plus seeded changes that shrink by 0.3 per corrector (a
+    stand-in for the momentum predictor's output as the SIMPLE/PISO
+    iterations of the step converge)."""
+    import numpy as np
+
+    import cases
+    rng = np.random.default_rng(seed)
+    mesh = dict(xf=case.xf, Sf=case.Sf, spacing=(4.0 / case.dims[1],) * 3, dims=case.dims)
+    out = [case.phi]
+    for k in range(1, n_solves):
+        out.append(case.phi + 0.02 * 0.3 ** k * cases.random_face_flux(mesh, rng, two_d=case.dims[2] == 1))
+    return np.stack(out)
+
+
+def measure_piso(steps, warmup, dev, stream, flush, n_outer=6, n_corr=2):
+    """The pressure part of one time step of the segregated solver (Sec. 4.1.1:
+    6 outer iterations x 2 correctors) on the 1024x512 tank: gfm_piso_step
+    (12 warm-started mixed solves on one alpha, then the corrected flux,
+    gradient and velocity) captured once in a CUDA graph and replayed; next
+    to it the same 12 solves as cold, separate assemble + solve calls."""
+    import torch
+
+    import cases
+    import paper_1804_01130_gb300 as g
+    c = cases.make_case(2)
+    k = n_outer * n_corr
+    h = g.GFM.from_case(c, renumber=RENUMBER["tank2d"])
+    alpha = torch.as_tensor(c.alpha, device=dev)
+    phis = torch.as_tensor(piso_fluxes(c, k), device=dev).contiguous()
+    p = torch.zeros(c.n, dtype=torch.float64, device=dev)
+    info = torch.zeros(4 * k, dtype=torch.float64, device=dev)
+    fl = torch.empty(c.F, dtype=torch.float64, device=dev)
+    G = torch.empty((3, c.n), dtype=torch.float64, device=dev)
+    U = torch.empty((3, c.n), dtype=torch.float64, device=dev)
+    V = torch.as_tensor(c.V, device=dev)
+    phys = dict(rho_w=c.rho_w, rho_a=c.rho_a, g=c.g, ref_cell=c.ref_cell, ref_value=c.ref_value)
+    rtol = WORKLOADS["tank2d"]["rtol"]
+    h.assemble(alpha, phis[0], **phys)
+    h.autotune(mode="mixed", rtol=rtol, inner_rtol=INNER_RTOL, trials=2)
+
+    def enqueue(st=None):
+        h.piso_step(alpha, phis, p, info, V=V, phi_corr=fl, grad=G, U=U, rtol=rtol, inner_rtol=INNER_RTOL,
+                    stream=st, **phys)
+
+    enqueue()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    l0 = h.profile().launches_total
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            enqueue(side)
+    torch.cuda.current_stream().wait_stream(side)
+    per_replay = h.profile().launches_total - l0
+    for i in range(warmup):
+        flush.fill_(float(i))
+        graph.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(100 + i))
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clocks = clk.stop()
+    recs = h.infos_of_step(info, k)
+    its = [r.iters for r in recs]
+    # the same solves, cold and one call at a time
+    cold = []
+    for i in range(2):
+        flush.fill_(float(200 + i))
+        torch.cuda.synchronize()
+        a.record(stream)
+        for j in range(k):
+            h.assemble(alpha, phis[j], **phys)
+            h.solve(mode="mixed", rtol=rtol, inner_rtol=INNER_RTOL, info_on_device=True, out=p)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cold.append(a.elapsed_time(b))
+    cold_its = []
+    for j in range(k):
+        h.assemble(alpha, phis[j], **phys)
+        _, _, inf = h.solve(mode="mixed", rtol=rtol, inner_rtol=INNER_RTOL)
+        cold_its.append(inf.iters)
+    ms_step = statistics.mean(ms)
+    h.close()
+    return {
+        "metric": "pressure part of one time step (6 outer x 2 correctors) under one CUDA graph",
+        "ms_per_time_step": ms_step, "solves_per_step": k, "ms_per_solve": ms_step / k,
+        "iters_per_solve": its, "all_converged": all(r.status == 0 for r in recs),
+        "cell_iters_per_s": c.n * sum(its) / (ms_step * 1e-3),
+        "cold_separate_calls_ms": statistics.mean(cold), "cold_iters_per_solve": cold_its,
+        "speedup_vs_cold_calls": statistics.mean(cold) / ms_step, "gpu_launches_per_step": per_replay,
+        "steps": steps, "warmup": warmup, "clocks": clocks,
+        "config": {"workload": WORKLOADS["tank2d"]["desc"], "rtol": rtol, "mode": "mixed",
+                   "fluxes": "case flux + seeded changes shrinking 0.3x per corrector (synthetic)",
+                   "outputs": "corrected flux, (1/rho) grad p_d and cell velocity of the last corrector"},
+    }
+
+
 def _make(key, dev, rank=0, world=1):
     return Batch64(key, dev, rank, world) if key == "batch64" else SingleMesh(key, dev)
 
@@ -761,6 +869,9 @@ def run_gfm(args, rank, local, world):
             subs[sub] = measure(sub, args.sub_steps, max(3, args.warmup), rank, world, dev, stream, flush,
                                 check_oracle=not args.no_oracle_check, with_e2e=True,
                                 cpu_seconds=0.0 if args.no_cpu_baseline else 4.0)
+        gc.collect()
+        torch.cuda.empty_cache()
+        subs["piso_tank2d"] = measure_piso(args.sub_steps, max(3, args.warmup), dev, stream, flush)
     if rank != 0:
         return
     line = {
