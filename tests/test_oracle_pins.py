@@ -76,7 +76,7 @@ def test_still_water_is_still_and_hydrostatic(nz, permute):
     p, fc, sy, info = oracle.solve(c, direct=True)
     q = oracle.corrected_flux(c, fc, p)
     scale = np.max(np.abs(fc.gamma * fc.jump))
-    # corrected flux vanishes everywhere (L718-L721 balanced force)
+    # corrected flux vanishes everywhere (the balanced force stated after Eq. 20, Sec. 3.1)
     assert np.max(np.abs(q)) <= 1e-12 * scale
     wet = c.alpha >= 0.5
     Kw, Ka = p[wet], p[~wet]
