@@ -662,7 +662,7 @@ __device__ __forceinline__ double apply64_diag(const Sell &m, Row rw, int lane, 
 // L1 residual sum|r| / (sum|A x - x_avg rowsum| + sum|b - x_avg rowsum|),
 // and the result record.  bnorm is only meaningful in thread 0.
 template <int CH>
-__device__ void finish(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, int iters, int refinements,
+__device__ __noinline__ void finish(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, int iters, int refinements,
                        int status, double bnorm)
 {
     const int n = a.m.n;
@@ -1202,8 +1202,9 @@ namespace {
 // `zero_p` the kept direction up.y is cleared.  Thread 0 gets
 // t = (||r||^2 in FP64, r32.u, r32.r32) and sh.y = Z^T r32.
 template <int CH>
-__device__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, float2 *up, double sc,
-                                 double isc, bool fold, bool zero_p, double (&t)[3], double &y_lane)
+__device__ __noinline__ bool replace_residual(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, float2 *up,
+                                              double sc, double isc, bool fold, bool zero_p, double (&t)[3],
+                                              double &y_lane)
 {
     const int n = a.m.n;
     const int ref = a.prm->ref;
@@ -1416,6 +1417,11 @@ __device__ __forceinline__ void mixed_op_group_hoisted(const TabT &tab, int sb, 
 
 }  // namespace
 
+struct T0State {
+    double bnorm, gam, gam_prev, rho_max, best_rel2, rho_stop;
+    int stall, last_upd;
+};
+
 template <int CH, bool STREAM, bool CT = false>
 __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 {
@@ -1466,9 +1472,23 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
     block_sum_f64<1>(sh, vb);
     double tb[1];
     if (!grid_allreduce<1>(g, sh, vb, tb)) { bail(); return; }
-    // thread-0 scalar state (last_upd: iteration of the last residual replacement)
-    double bnorm = 1.0, gam = 0.0, gam_prev = 1.0, rho_max = 0.0, best_rel2 = 0.0, rho_stop = 0.0;
-    int stall = 0, last_upd = 0;
+    // thread-0 scalar state (last_upd: iteration of the last residual
+    // replacement), kept in shared memory rather than in every thread's
+    // registers, which the operator pass needs for its gathers in flight
+    __shared__ T0State t0s;
+    double &bnorm = t0s.bnorm, &gam = t0s.gam, &gam_prev = t0s.gam_prev, &rho_max = t0s.rho_max,
+           &best_rel2 = t0s.best_rel2, &rho_stop = t0s.rho_stop;
+    int &stall = t0s.stall, &last_upd = t0s.last_upd;
+    if (threadIdx.x == 0) {
+        bnorm = 1.0;
+        gam = 0.0;
+        gam_prev = 1.0;
+        rho_max = 0.0;
+        best_rel2 = 0.0;
+        rho_stop = 0.0;
+        stall = 0;
+        last_upd = 0;
+    }
     if (threadIdx.x == 0) {
         bnorm = (tb[0] > 0.0) ? sqrt(tb[0]) : 1.0;
         // one power-of-two scale for the whole solve, from ||b||: residual
