@@ -101,6 +101,9 @@ def _args():
                     help="no timing: one short mixed and one short FP64 solve (batch64: one batched solve) "
                          "for a profiler")
     ap.add_argument("--profile-iters", type=int, default=300)
+    ap.add_argument("--profile-launch", default=None,
+                    help="threads,ctas_per_sm,form of the profiled solve instead of the autotuner's trials (so that "
+                         "the profiler's first solver launch is the one of interest)")
     return ap.parse_args()
 
 
@@ -130,9 +133,10 @@ def _cores() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
-def _traffic_record(workload: str):
+def _traffic_record(workload: str, kernel: str):
     """DRAM bytes per launch of the solver kernel from a committed ncu summary,
-    valid only while the kernel source is unchanged (else None)."""
+    valid only while the kernel source is unchanged and the capture is of the
+    kernel the bench ran (else None)."""
     src = os.path.join(ROOT, "paper_1804_01130_gb300", "csrc", "gfm_solve.cu")
     with open(src, "rb") as fh:
         sha = hashlib.sha256(fh.read()).hexdigest()[:16]
@@ -141,7 +145,7 @@ def _traffic_record(workload: str):
         with open(path) as fh:
             rec = json.load(fh)
         r = rec.get(workload, {})
-        if r.get("source_sha") == sha:
+        if r.get("source_sha") == sha and kernel in r.get("kernel", ""):
             return r, sha
     except Exception:
         pass
@@ -269,9 +273,14 @@ class SingleMesh:
         # launch shape picked by the library's autotuner on this system
         self.h.assemble(self.alpha, self.phi, **self.phys)
         thr, per_sm, _ = self.h.autotune(mode="mixed", rtol=self.rtol, inner_rtol=INNER_RTOL, trials=2)
+        # the iteration form the autotuner kept: two passes and two all-reduces per
+        # FP32 iteration (k_solve_mixed) or one fused pass and one (k_solve_fused)
+        form = self.h.iteration_form()
+        self.kernel = "k_solve_fused" if form == 2 else "k_solve_mixed"
         self.config = {"cells": c.n, "faces": c.F, "rtol": self.rtol, "inner_rtol": INNER_RTOL, "mode": "mixed",
                        "renumber": RENUMBER_NAME[RENUMBER[key]],
-                       "launch": {"threads": thr, "ctas_per_sm": per_sm, "autotuned": True}}
+                       "launch": {"threads": thr, "ctas_per_sm": per_sm, "autotuned": True,
+                                  "form": "fused" if form == 2 else "two-pass"}}
 
     def close(self):
         self.h.close()
@@ -812,15 +821,16 @@ def measure(key, steps, warmup, rank, world, dev, stream, flush, *, check_oracle
     kms = statistics.mean(kernel_ms)
     achieved = by / (kms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    trec, sha = _traffic_record(key)
+    kname = getattr(w, "kernel", "k_solve_batched" if key == "batch64" else "k_solve_mixed")
+    trec, sha = _traffic_record(key, kname)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (trec["dram_bytes_per_launch"] if trec else None),
-            "kernel": "k_solve_batched" if key == "batch64" else "k_solve_mixed", "kernel_ms": kms,
+            "kernel": kname, "kernel_ms": kms,
             "peak_kind": peak_kind, "frac_of_spec_8000_gbs": achieved / 8000.0,
             "algorithmic_bytes_per_launch": by, "solver_source_sha": sha,
             "bytes_model": "(52 + 12 F/n) B per cell-iteration + (24 + 16 F/n) B per cell per FP64 replacement"}
     if trec is None:
-        roof["traffic_note"] = "no DRAM capture on the current solver source"
+        roof["traffic_note"] = "no DRAM capture of this kernel on the current solver source"
     if key == "tank2d":
         roof["l2_resident"] = True
         roof["note"] = ("the tank's FP32 working set (~35 MB) stays in the 129 MB L2 across iterations, so this "
@@ -906,7 +916,11 @@ def profile_run(args):
                    torch.as_tensor(np.concatenate([t.phi for t in tanks])),
                    [dict(rho_w=t.rho_w, rho_a=t.rho_a, g=t.g, ref_cell=t.ref_cell, ref_value=t.ref_value)
                     for t in tanks])
-        b.autotune(rtol=WORKLOADS["batch64"]["rtol"], inner_rtol=INNER_RTOL, trials=1)  # the bench's launch shape
+        if args.profile_launch:
+            t, c, _ = (int(x) for x in args.profile_launch.split(","))
+            b.set_tuning(threads=t, ctas_per_sm=c)
+        else:
+            b.autotune(rtol=WORKLOADS["batch64"]["rtol"], inner_rtol=INNER_RTOL, trials=1)  # the bench's launch shape
         _, _, infos = b.solve(rtol=WORKLOADS["batch64"]["rtol"], max_iters=args.profile_iters, raise_on_error=False)
         print("batched", max(i.iters for i in infos), flush=True)
         torch.cuda.synchronize()
@@ -915,7 +929,10 @@ def profile_run(args):
     s = g.GFM.from_case(case, renumber=RENUMBER[args.profile_run])
     s.assemble(torch.as_tensor(case.alpha), torch.as_tensor(case.phi), case.rho_w, case.rho_a, case.g,
                case.ref_cell)
-    if args.profile_iters >= 100000:  # a full solve: the bench's autotuned launch shape
+    if args.profile_launch:
+        t, c, f = (int(x) for x in args.profile_launch.split(","))
+        s.set_tuning(threads=t, ctas_per_sm=c, form=f)
+    elif args.profile_iters >= 100000:  # a full solve: the bench's autotuned launch shape
         s.autotune(mode="mixed", rtol=WORKLOADS[args.profile_run]["rtol"], inner_rtol=INNER_RTOL, trials=1)
     for mode in ("mixed", "fp64"):
         _, _, info = s.solve(mode=mode, rtol=1e-10, max_iters=args.profile_iters, raise_on_error=False)

@@ -144,6 +144,10 @@ typedef struct {
 typedef struct {
     int32_t threads;     /* threads per CTA (multiple of 32, <= 512)        */
     int32_t ctas_per_sm; /* co-resident CTAs per SM (grid = SMs x this)     */
+    int32_t form;        /* GFM_MIXED iteration form: 1 = two passes and two
+                          * grid all-reduces per FP32 iteration (default);
+                          * 2 = one fused pass and one all-reduce (single
+                          * meshes only); see gfm_set_tuning              */
 } gfm_tuning;
 
 /* Timings of the last call, recorded with CUDA events on the launching
@@ -466,8 +470,20 @@ gfm_status gfm_set_table(gfm_handle h, int32_t compact, int32_t force_stream);
 gfm_status gfm_get_table(gfm_handle h, int32_t *compact_usable, int32_t *n_classes, int32_t *compact_valid);
 
 /* Launch shape of the persistent kernels (threads a multiple of 32, at most
- * 512).  threads = 0 / ctas_per_sm = 0 keep the current value.  Errors:
- * GFM_ERR_ARG if the shape is out of range or cannot be co-resident. */
+ * 512) and the form of the mixed-precision iteration.  A zero field keeps
+ * the current value.  Both forms run the same preconditioned CG recurrences
+ * of the pinned system of Sec. 3.1 (the paper names no solver) with the same
+ * FP64 residual replacement and stopping rules.  Form 1 applies each FP32
+ * iteration as an operator pass (p = u + beta p, s = A p, p.s) and an update
+ * pass (x, r, u; r.u, r.r), each closed by a grid all-reduce.  Form 2 keeps
+ * per cell (q = D^{-1} r, t = D^{-1} s, p) and folds the update into the
+ * next operator pass, every neighbour's new direction recomputed from its
+ * gathered state; r.u of the next step follows from q.D q, t.D q and t.D t
+ * (summed with p.s in the same all-reduce), so an iteration closes with ONE
+ * all-reduce.  Form 2 suits meshes whose iteration is bound by all-reduce
+ * latency; the results agree within the solver tolerance, not bit for bit.
+ * Errors: GFM_ERR_ARG if the shape is out of range or cannot be co-resident,
+ * or form 2 is asked of a batched handle. */
 gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t);
 gfm_status gfm_get_tuning(gfm_handle h, gfm_tuning *t);
 
@@ -475,7 +491,8 @@ gfm_status gfm_get_tuning(gfm_handle h, gfm_tuning *t);
  * Autotuner: on the assembled system, time `trials` solves (median, CUDA
  * events on `stream`) with opts for each launch shape of the persistent
  * kernel ({512,1}, {256,2}, {128,4}, {384,1}, {256,1} threads x CTAs per
- * SM, where co-resident).  For a batched handle it also tries the tank->CTA
+ * SM, where co-resident), and for a single mesh in GFM_MIXED mode with both
+ * iteration forms (gfm_set_tuning).  For a batched handle it also tries the tank->CTA
  * table weighted by the iterations each tank took (tanks that iterate longer
  * get more CTAs).  The fastest shape and table are kept for later solves and
  * returned in *chosen and *best_ms (either may be NULL).  The paper has no

@@ -69,7 +69,7 @@ class _Info(ct.Structure):
 
 
 class _Tuning(ct.Structure):
-    _fields_ = [("threads", ct.c_int32), ("ctas_per_sm", ct.c_int32)]
+    _fields_ = [("threads", ct.c_int32), ("ctas_per_sm", ct.c_int32), ("form", ct.c_int32)]
 
 
 class _Profile(ct.Structure):
@@ -421,14 +421,21 @@ class GFM:
                     "gfm_nonorth_correct")
         return corr
 
-    def set_tuning(self, threads=0, ctas_per_sm=0):
-        self._check(self.lib.gfm_set_tuning(self.h, ct.byref(_Tuning(int(threads), int(ctas_per_sm)))),
+    def set_tuning(self, threads=0, ctas_per_sm=0, form=0):
+        """Launch shape and mixed iteration form (1: two passes, 2: fused); 0 keeps a value."""
+        self._check(self.lib.gfm_set_tuning(self.h, ct.byref(_Tuning(int(threads), int(ctas_per_sm), int(form)))),
                     "gfm_set_tuning")
 
     def get_tuning(self):
         t = _Tuning()
         self._check(self.lib.gfm_get_tuning(self.h, ct.byref(t)), "gfm_get_tuning")
         return t.threads, t.ctas_per_sm
+
+    def iteration_form(self) -> int:
+        """The mixed iteration form in use: 1 (two passes per iteration) or 2 (fused, one all-reduce)."""
+        t = _Tuning()
+        self._check(self.lib.gfm_get_tuning(self.h, ct.byref(t)), "gfm_get_tuning")
+        return t.form
 
     def autotune(self, mode="mixed", rtol=1e-10, inner_rtol=1e-4, trials=3, timeout_ms=2000.0, stream=None):
         """Time the launch shapes (and, batched, the iteration-weighted tank table) on the assembled

@@ -35,6 +35,7 @@ struct gfm_ctx {
     double *b = nullptr, *diag = nullptr, *dinv = nullptr, *x64 = nullptr, *r64 = nullptr;
     double *p64 = nullptr, *q64 = nullptr, *rhs = nullptr, *tmp_user = nullptr, *tmp_user2 = nullptr;
     float2 *UP0 = nullptr, *UP1 = nullptr;
+    float4 *Q0 = nullptr, *Q1 = nullptr;  // fused form: (q, t, p, region) per cell
     float *P32 = nullptr;
     float *R32 = nullptr, *S32 = nullptr, *E = nullptr, *dinv32 = nullptr;
     // two-level preconditioner (coarse space of connected one-phase regions)
@@ -90,7 +91,7 @@ struct gfm_ctx {
     bool assembled = false;
     gfm_phys phys{};
     int ref_internal = -1;
-    gfm_tuning tuning{512, 1};
+    gfm_tuning tuning{512, 1, 1};
     bool profiling = false;
     gfm_profile prof{};
     cudaEvent_t ev[6] = {};
@@ -129,7 +130,7 @@ void free_all(gfm_ctx *h)
     void *ptrs[] = {h->owner, h->neighbour, h->Sf, h->C, h->perm, h->iperm, h->slice_ptr, h->col, h->face,
                     h->val64, h->val32, h->lambda, h->gamma, h->jump, h->sigma, h->phi, h->dl_dlam, h->kind,
                     h->alpha, h->b, h->diag, h->dinv, h->x64, h->r64, h->p64, h->q64, h->rhs, h->tmp_user,
-                    h->tmp_user2, h->UP0, h->UP1, h->P32, h->R32, h->S32, h->E, h->dinv32, h->stage_alpha,
+                    h->tmp_user2, h->UP0, h->UP1, h->Q0, h->Q1, h->P32, h->R32, h->S32, h->E, h->dinv32, h->stage_alpha,
                     h->stage_phi, h->stage_p, h->prm, h->bar,
                     h->err, h->partials, h->dinfo, h->cc_parent, h->cc_size, h->cc_cand, h->cc_counters,
                     h->cc_bcount, h->cc_boff, h->cc_epart,
@@ -182,6 +183,7 @@ struct LaunchPlan {
     int grid = 0, threads = 0, cache_cap = 0, meta_slots = 0;
     int n_stages = 0, stage_slices = 0, stage_cap = 0;  // streamed tables (MIXED), 0 = not streamed
     bool ct = false;                                  // the stages hold the compact table
+    bool fused = false;                               // MIXED: the one-pass, one-all-reduce form
     size_t dyn = 0;
 };
 
@@ -189,7 +191,10 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
 {
     const int t = h->tuning.threads;
     int per = h->tuning.ctas_per_sm;
-    const void *k = h->batched ? gfm::batched_kernel(h->ht.max_width) : gfm::solver_kernel(mode, h->ht.max_width, t);
+    // the fused form (single meshes, MIXED) never uses the compact table
+    const bool fused = !h->batched && mode == gfm::Mode::MIXED && h->tuning.form == 2;
+    const void *k = h->batched ? gfm::batched_kernel(h->ht.max_width)
+                               : gfm::solver_kernel(mode, h->ht.max_width, t, false, false, fused);
     cudaFuncAttributes fa;
     GFM_CUDA(h, cudaFuncGetAttributes(&fa, k));
     int occ0 = 0;
@@ -242,7 +247,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     int n_stages = 0, stage_slices = 0, stage_cap = 0;
     // the compact table streams 4 bytes per slot instead of 8, and stages
     // its dictionary after the ring
-    const bool ct = mode == gfm::Mode::MIXED && h->ent_valid && h->ct_pref;
+    const bool ct = mode == gfm::Mode::MIXED && h->ent_valid && h->ct_pref && !fused;
     const long long sbytes = ct ? 4 : 8;
     const long long dict_bytes = ct ? ((long long)(2 * h->n_cls + 1) * 4 + 15) / 16 * 16 : 0;
     if (mode == gfm::Mode::MIXED && cap < max_slots) {
@@ -264,7 +269,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
                                 (n_stages ? (long long)n_stages * stage_cap * sbytes + dict_bytes : cap * slot_bytes));
     if (n_stages)
         k = h->batched ? gfm::batched_kernel(h->ht.max_width, true, ct)
-                       : gfm::solver_kernel(mode, h->ht.max_width, t, true, ct);
+                       : gfm::solver_kernel(mode, h->ht.max_width, t, true, ct, fused);
     GFM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int occ = 0;
     GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, t, dyn));
@@ -277,6 +282,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
     lp->stage_slices = stage_slices;
     lp->stage_cap = stage_cap;
     lp->ct = ct && n_stages > 0;
+    lp->fused = fused;
     lp->dyn = dyn;
     return GFM_OK;
 }
@@ -328,6 +334,8 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
     a.q64 = h->q64;
     a.UP0 = h->UP0;
     a.UP1 = h->UP1;
+    a.Q0 = h->Q0;
+    a.Q1 = h->Q1;
     a.P32 = h->P32;
     a.R32 = h->R32;
     a.S32 = h->S32;
@@ -354,7 +362,7 @@ gfm_status enqueue_solve(gfm_ctx *h, const gfm_solve_opts *o, const double *rhs,
     a.partials = h->partials;
     a.info = info_dev;
     gfm::BatchArgs ba{};
-    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads, lp.n_stages > 0, lp.ct);
+    const void *kernel = gfm::solver_kernel(mode, h->ht.max_width, threads, lp.n_stages > 0, lp.ct, lp.fused);
     if (h->batched) {
         a.n_per_tank = h->tncell;
         a.prm = h->tprm;
@@ -456,10 +464,10 @@ gfm_status alloc_upload(gfm_ctx *h, cudaStream_t s)
     A(val64, ns); A(val32, ns);
     A(lambda, F); A(gamma, F); A(jump, F); A(sigma, F); A(phi, F); A(dl_dlam, F); A(kind, F);
     A(alpha, n); A(b, np); A(diag, np); A(dinv, np); A(x64, np); A(r64, np); A(p64, np); A(q64, np);
-    A(rhs, np); A(tmp_user, n); A(tmp_user2, n); A(UP0, np); A(UP1, np); A(P32, np); A(R32, np); A(S32, np); A(E, np);
+    A(rhs, np); A(tmp_user, n); A(tmp_user2, n); A(UP0, np); A(UP1, np); A(Q0, np); A(Q1, np); A(P32, np); A(R32, np); A(S32, np); A(E, np);
     A(dinv32, np);
     A(stage_alpha, n); A(stage_phi, F); A(stage_p, n);
-    A(prm, 1); A(bar, 1); A(err, 1); A(partials, 2 * (size_t)h->max_grid * 12); A(dinfo, 1);
+    A(prm, 1); A(bar, 1); A(err, 1); A(partials, 2 * (size_t)h->max_grid * gfm::kMaxReduce); A(dinfo, 1);
     h->max_cross = (int)std::min<long long>((long long)F, std::max<long long>(65536, (long long)F / 8));
     A(cc_parent, n); A(cc_size, n); A(cc_cand, gfm::kMaxCandidates); A(cc_counters, 2);
     A(cc_bcount, (F + 255) / 256); A(cc_boff, (F + 255) / 256);
@@ -485,6 +493,8 @@ gfm_status alloc_upload(gfm_ctx *h, cudaStream_t s)
     if (e == cudaSuccess) e = cudaMemsetAsync(h->coarse, 0, sizeof(gfm::Coarse), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->UP0, 0, sizeof(float2) * np, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->UP1, 0, sizeof(float2) * np, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Q0, 0, sizeof(float4) * np, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Q1, 0, sizeof(float4) * np, s);
     float *zero_f[] = {h->R32, h->S32, h->E, h->dinv32};
     for (float *zp : zero_f)
         if (e == cudaSuccess) e = cudaMemsetAsync(zp, 0, sizeof(float) * np, s);
@@ -1366,8 +1376,11 @@ gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t)
     gfm_tuning nt = h->tuning;
     if (t->threads) nt.threads = t->threads;
     if (t->ctas_per_sm) nt.ctas_per_sm = t->ctas_per_sm;
+    if (t->form) nt.form = t->form;
     if (nt.threads < 32 || nt.threads > gfm::solver_max_threads() || nt.threads % 32 || nt.ctas_per_sm < 1)
         return fail(h, GFM_ERR_ARG, "threads must be a multiple of 32 in [32, 1024], ctas_per_sm >= 1");
+    if (nt.form != 1 && nt.form != 2) return fail(h, GFM_ERR_ARG, "form must be 1 (two passes) or 2 (fused)");
+    if (nt.form == 2 && h->batched) return fail(h, GFM_ERR_ARG, "the batched solve has the two-pass form only");
     if (h->sm_count * nt.ctas_per_sm > h->max_grid) return fail(h, GFM_ERR_ARG, "grid larger than workspace");
     const gfm_tuning old = h->tuning;
     h->tuning = nt;
@@ -1378,7 +1391,7 @@ gfm_status gfm_set_tuning(gfm_handle h, const gfm_tuning *t)
     }
     for (gfm::Mode m : {gfm::Mode::FP64, gfm::Mode::MIXED}) {
         int occ = 0;
-        const void *k = gfm::solver_kernel(m, h->ht.max_width, nt.threads);
+        const void *k = gfm::solver_kernel(m, h->ht.max_width, nt.threads, false, false, nt.form == 2);
         GFM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nt.threads, 0));
         LaunchPlan lp;
         if (occ < nt.ctas_per_sm || plan_launch(h, m, &lp) != GFM_OK) {
@@ -1442,7 +1455,12 @@ gfm_status gfm_autotune(gfm_handle h, const gfm_solve_opts *opts, int32_t trials
     const std::vector<double> start_w = h->bweight;
     // shapes within 512 threads' worth of registers per SM (the solvers use
     // 128 registers a thread)
-    const gfm_tuning cands[] = {{512, 1}, {256, 2}, {128, 4}, {384, 1}, {256, 1}};
+    const int shapes[][2] = {{512, 1}, {256, 2}, {128, 4}, {384, 1}, {256, 1}};
+    std::vector<gfm_tuning> cands;
+    // a single mesh in MIXED mode also tries the fused form with every shape
+    const int n_forms = (!h->batched && opts->mode == GFM_MIXED) ? 2 : 1;
+    for (int f = 1; f <= n_forms; ++f)
+        for (const auto &sh : shapes) cands.push_back(gfm_tuning{sh[0], sh[1], f});
     gfm_tuning best = start;
     std::vector<double> best_w = start_w;
     float best_t = 0.0f;

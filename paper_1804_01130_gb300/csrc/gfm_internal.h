@@ -44,6 +44,7 @@ struct Coarse {
 // Z^T A Z of those regions and its inverse, and the tank's stretch
 // [x0, x1) of the face-ordered cross-face list.
 constexpr int kTankCoarse = 2;
+constexpr int kMaxReduce = 16;  // most values one grid all-reduce of a single mesh sums
 constexpr int kBatchNR = 3 + kTankCoarse;  // most values one batched all-reduce sums
 constexpr int kLaneSum = 8;                // tanks with more CTAs are summed by a warp
 // bytes of dynamic shared memory ahead of the batched solve's tables: the
@@ -114,6 +115,7 @@ struct SolveArgs {
     float2 *UP0, *UP1;     // MIXED: (u, p) pairs, double-buffered (gathered)
     float *R32, *S32, *E;  // MIXED: scaled residual, s = A p, FP32 correction
     float *P32;            // MIXED: this iteration's direction p (written whole, read by the update pass)
+    float4 *Q0, *Q1;       // MIXED, fused form: (q, t, p, region) per cell, double-buffered (gathered)
     const float *dinv32;   // MIXED: 1 / (float)diag
     const int32_t *iperm;  // [n] internal -> caller index
     double *p_user;        // caller-order x0 in / solution out
@@ -307,7 +309,8 @@ struct BatchArgs {
 const void *batched_kernel(int max_width, bool streamed = false, bool compact = false);
 
 enum class Mode { FP64 = 0, MIXED = 1 };
-const void *solver_kernel(Mode m, int max_width, int threads, bool streamed = false, bool compact = false);
+const void *solver_kernel(Mode m, int max_width, int threads, bool streamed = false, bool compact = false,
+                          bool fused = false);
 int solver_max_threads();
 
 }  // namespace gfm

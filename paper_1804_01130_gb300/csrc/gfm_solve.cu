@@ -72,7 +72,7 @@ __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
 
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(const volatile int *)p; }
 
-constexpr int kMaxNR = 12;
+constexpr int kMaxNR = kMaxReduce;  // the partials buffer is [2][kMaxNR][grid]
 
 // Values decided by thread 0 and broadcast to the CTA.
 struct Ctl {
@@ -91,6 +91,7 @@ struct Shared {
     double y[kMaxCoarse];    // thread 0: Z^T r (coarse components of the residual)
     double c64[kMaxCoarse];  // coarse correction E^{-1} Z^T r, broadcast
     float c32[kMaxCoarse];
+    float cz[kMaxCoarse + 1];  // fused form: 0, then the FP32 coarse correction of each region
     float zb32[kMaxCoarse];  // this CTA's Z^T (A p) in a pass
     double zb64[kMaxCoarse];
     float zbw32[16][kMaxCoarse];  // the same per warp, summed in warp order
@@ -161,6 +162,7 @@ template <int NR>
 __device__ __forceinline__ bool grid_allreduce(Grid &g, Shared &sh, const double (&blk)[NR], double (&out)[NR],
                                                int nr = NR)
 {
+    static_assert(NR <= kMaxNR, "grid reduction buffer too small");
     int e = 0;
     __syncthreads();
     g.epoch += 1u;
@@ -1721,6 +1723,454 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Mixed precision, fused form: ONE operator pass and ONE grid all-reduce per
+// FP32 iteration.
+//
+// The two-pass iteration needs two grid-wide all-reduces (p.s, then r.u),
+// and on a mesh whose vectors stay in L2 those cost more than the passes.
+// Here the update of iteration k is folded into the operator pass of
+// iteration k + 1.  Each cell keeps the state (q, t, p, region), with
+// q = D^{-1} r the Jacobi part of the preconditioned residual and
+// t = D^{-1} s, s = A p.  Given alpha_k, beta_{k+1} and the coarse
+// correction c_{k+1} = E^{-1} Z^T r_{k+1}, one pass forms, for the cell and,
+// from their gathered state, for its neighbours,
+//     q' = q - alpha t,   u' = q' + c[region],   p' = u' + beta p,
+// then s' = A p' (difference form), t' = s' / D and e += alpha p.  Its
+// partial sums are p'.s' (for alpha), q'.D q' = r'.D^{-1} r' (for r'.u'),
+// t'.D q' and t'.D t' (so that r''.D^{-1} r'' after the next step, and with
+// it beta, follows from alpha without another all-reduce), r'.r' (the
+// stopping and replacement tests) and Z^T A p' (the coarse recurrence).  A
+// neighbour's p' is recomputed with the same operations as its owner's, so
+// both sides of a face use the same bits.  Residual replacement, restarts
+// and the stopping rules are those of the two-pass form.
+// ---------------------------------------------------------------------------
+namespace {
+
+// p' of a cell from its stored state (q, t, p, region bits).
+__device__ __forceinline__ float fused_pnew(float4 v, float al, float be, const Shared &sh)
+{
+    const float qn = fmaf(-al, v.y, v.x);
+    return fmaf(be, v.z, __fadd_rn(qn, sh.cz[__float_as_int(v.w) + 1]));
+}
+
+// One group of the fused pass: slices sb, sb + nw, ... (U of them, those
+// before s_end); acc gets p'.s', q'.D q', t'.D q', t'.D t', r'.r'.
+template <int CH, int U, typename TabT>
+__device__ __forceinline__ void fused_group(const TabT &tab, int sb, int s_end, const Range &R, int n,
+                                            const float4 *__restrict__ cur, float4 *__restrict__ nxt,
+                                            float *__restrict__ E, const float *__restrict__ dinv, float al, float be,
+                                            int ref, float pin32, int rc, int K, Shared &sh, FF (&acc)[5])
+{
+    int ii[U], base[U], w[U];
+    float4 v[U];
+    float pn[U], si[U], di[U], ei[U];
+    int wmax = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int s = sb + u * R.nw;
+        ii[u] = s * kSlice + R.lane;
+        base[u] = 0;
+        w[u] = 0;
+        const bool act = s < s_end && ii[u] < n;
+        if (act) {
+            const Row rw = tab.row(s);
+            base[u] = rw.base;
+            w[u] = rw.w;
+        }
+        // the cell's own loads all in flight together, before the gathers
+        v[u] = act ? cur[ii[u]] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        di[u] = act ? __ldcs(dinv + ii[u]) : 0.0f;
+        ei[u] = act ? __ldcs(E + ii[u]) : 0.0f;
+        wmax = max(wmax, w[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        pn[u] = fused_pnew(v[u], al, be, sh);
+        si[u] = (ii[u] == ref) ? pin32 * pn[u] : 0.0f;
+    }
+    for (int k0 = 0; k0 < wmax; k0 += CH) {
+        float4 vj[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const bool ok = k0 + c < w[u];
+                vj[u][c] = ok ? cur[tab.c(base[u] + (k0 + c) * kSlice + R.lane, ii[u])] : v[u];
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float gm = (k0 + c < w[u]) ? tab.v(base[u] + (k0 + c) * kSlice + R.lane) : 0.0f;
+                si[u] = fmaf(gm, pn[u] - fused_pnew(vj[u][c], al, be, sh), si[u]);
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (sb + u * R.nw < s_end && ii[u] < n) {
+            const float qn = fmaf(-al, v[u].y, v[u].x);
+            const float tn = si[u] * di[u];
+            nxt[ii[u]] = make_float4(qn, tn, pn[u], v[u].w);
+            __stcs(E + ii[u], fmaf(al, v[u].z, ei[u]));
+            const float rn = qn * __frcp_rn(di[u]);  // r' = D q'
+            ff_add(acc[0], pn[u] * si[u]);
+            ff_add(acc[1], rn * qn);
+            ff_add(acc[2], si[u] * qn);
+            ff_add(acc[3], si[u] * tn);
+            ff_add(acc[4], rn * rn);
+            if (ii[u] == ref && rc >= 0 && K > 0) sh.zpin32 = pin32 * pn[u];  // pin term of Z^T A p'
+        }
+    }
+}
+
+// Residual replacement of the fused form.  When `fold`, first x += e / sc in
+// FP64 (e = 0).  Then r = b - A x in FP64, r32 = (float)(r sc) and
+// q = r32 / D into the state; with `zero_p` the kept direction p and its t
+// are cleared.  Every thread gets t = (||r||^2 in FP64, q.D q, t.D q, r32.r32)
+// and lane k of warp 0 the k-th component of Z^T r32.
+template <int CH>
+__device__ __noinline__ bool replace_fused(const SolveArgs &a, Grid &g, Shared &sh, const Range &R, float4 *qd,
+                                           double sc, double isc, bool fold, bool zero_p, double (&t)[4],
+                                           double &y_lane)
+{
+    const int n = a.m.n;
+    const int ref = a.prm->ref;
+    const int K = a.coarse->K;
+    const double pin64 = a.prm->pin64;
+    double *x = a.x64;
+    if (fold) {
+        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+            const int i = s * kSlice + R.lane;
+            if (i < n) {
+                x[i] = fma((double)a.E[i], isc, x[i]);
+                a.E[i] = 0.0f;
+            }
+        }
+        if (!grid_sync(g, sh)) return false;  // x complete
+    }
+    double vr[1] = {0.0};
+    FF acc[3 + kMaxCoarse];
+    for (int k = 0; k < 3 + kMaxCoarse; ++k) acc[k] = FF{0.f, 0.f};
+    for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+        const int i = s * kSlice + R.lane;
+        if (i < n) {
+            const double xi = x[i];
+            const double ri = a.b[i] - apply64_diff<CH>(a.m, row_of(a.m, s), R.lane, x, xi, i == ref ? pin64 : 0.0);
+            vr[0] = fma(ri, ri, vr[0]);
+            const float r32 = (float)(ri * sc);
+            const float q = r32 * a.dinv32[i];
+            const int cm = a.comp[i];
+            float4 v = zero_p ? make_float4(q, 0.0f, 0.0f, __int_as_float(cm)) : qd[i];
+            v.x = q;
+            qd[i] = v;
+            ff_add(acc[0], r32 * q);
+            ff_add(acc[1], v.y * r32);
+            ff_add(acc[2], r32 * r32);
+#pragma unroll
+            for (int k = 0; k < kMaxCoarse; ++k) ff_add(acc[3 + k], (cm == k) ? r32 : 0.0f);
+        }
+    }
+    block_sum_f64<1>(sh, vr);
+    double ffo[3 + kMaxCoarse];
+    block_sum_ff<3 + kMaxCoarse>(sh, acc, ffo);
+    double blk[4 + kMaxCoarse], tt[4 + kMaxCoarse];
+    blk[0] = vr[0];
+    for (int k = 0; k < 3 + kMaxCoarse; ++k) blk[1 + k] = ffo[k];
+    // also the barrier after which the next pass gathers the new q
+    if (!grid_allreduce<4 + kMaxCoarse>(g, sh, blk, tt, 4 + K)) return false;
+    for (int k = 0; k < 4; ++k) t[k] = tt[k];  // every thread: the all-reduced values
+    if (threadIdx.x < 32) {
+        double yl = 0.0;  // lane k's component, picked without indexing the array at run time
+#pragma unroll
+        for (int k = 0; k < kMaxCoarse; ++k)
+            if (k == R.lane && k < K) yl = tt[4 + k];
+        y_lane = yl;
+    }
+    return true;
+}
+
+// Warp 0, K <= 8: y.c = sum over lanes k < K of y_k c_k in FP32 (lanes >= K
+// hold zeros, so three butterfly steps sum lanes 0..7), from lane 0 to all.
+__device__ __forceinline__ float coarse_dot8(int K, double y_lane, float c)
+{
+    float yc = ((threadIdx.x & 31) < K) ? (float)y_lane * c : 0.0f;
+    yc += __shfl_xor_sync(0xffffffffu, yc, 4);
+    yc += __shfl_xor_sync(0xffffffffu, yc, 2);
+    yc += __shfl_xor_sync(0xffffffffu, yc, 1);
+    return __shfl_sync(0xffffffffu, yc, 0);
+}
+
+// Warp 0: r.u of the state, q.D q plus the coarse part y.c with c = E^{-1} y
+// in FP32 (the correction the vectors use).  All lanes return the same value.
+__device__ __forceinline__ double fused_gamma(int K, double qdq, double y_lane, const Shared &sh)
+{
+    static_assert(kMaxCoarse <= 8, "coarse_dot8 sums at most 8 lanes");
+    return qdq + (double)coarse_dot8(K, y_lane, coarse32_lane(K, y_lane, sh));
+}
+
+// Warp 0: one step of the recurrences from state k (gam = r_k.u_k, ps, qdq,
+// tdq, tdt = the all-reduced p.s, q.D q, t.D q, t.D t of state k, zk_lane =
+// (Z^T A p_k)_lane): alpha_k = gam / p.s in FP32 (the vectors' precision, as
+// in the two-pass form), y_{k+1} = y_k - alpha_k Z^T A p_k (FP64),
+// c_{k+1} = E^{-1} y_{k+1} into sh.cz, r_{k+1}.u_{k+1} =
+// q.D q - 2 alpha t.D q + alpha^2 t.D t + y_{k+1}.c_{k+1} (FP64, where the
+// terms cancel) and beta_{k+1} = r_{k+1}.u_{k+1} / gam into sh.ctl.  With
+// `restart`, alpha = beta = 0 (the next direction is the preconditioned
+// residual).  A non-positive expanded r.u (rounding at a steep drop) also
+// sets beta = 0.  FP64 work is kept to a few instructions: GB300's FP64 pipe
+// makes each one cost as much as a long FP32 sequence.
+__device__ __forceinline__ void fused_advance(int K, double gam, double ps, double qdq, double tdq, double tdt,
+                                              double zk_lane, double &y_lane, bool restart, Shared &sh)
+{
+    const int lane = threadIdx.x & 31;
+    float al = 0.0f, be = 0.0f;
+    if (!restart) {
+        al = (float)gam / (float)ps;
+        if (lane < K) y_lane = fma(-(double)al, zk_lane, y_lane);
+    }
+    const float c = coarse32_lane(K, y_lane, sh);
+    if (!restart) {
+        const double ad = (double)al;
+        const double gn = fma(ad, fma(ad, tdt, -2.0 * tdq), qdq) + (double)coarse_dot8(K, y_lane, c);
+        be = (gn > 0.0 && isfinite(gn)) ? (float)gn / (float)gam : 0.0f;
+    }
+    if (lane < kMaxCoarse) sh.cz[1 + lane] = (lane < K) ? c : 0.0f;
+    if (lane == 0) {
+        sh.cz[0] = 0.0f;
+        sh.ctl.al = al;
+        sh.ctl.be = be;
+    }
+    __syncwarp();
+}
+
+}  // namespace
+
+// Thread-0 scalar state of the fused form, in shared memory.
+struct FusedState {
+    double bnorm, gam, rho_max, best_rel2, rho_stop;
+    double ps, tdt;  // p.s and t.D t of the last pass (kept across a replacement)
+    int stall, last_upd;
+};
+
+template <int CH, bool STREAM>
+__global__ void __launch_bounds__(512, 1) k_solve_fused(SolveArgs a)
+{
+    // slices per warp in one group: two for 4-face rows (22.9 -> 22.4 ms on
+    // the 1024x512 tank against one); with more faces the gathered state (16
+    // bytes, twice the two-pass form's pair) keeps fewer slices in flight
+    constexpr int U = CH <= 4 ? 2 : 8 / CH;
+    constexpr int US = CH <= 6 ? 2 : 1;
+    __shared__ Shared sh;
+    __shared__ FusedState fs;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
+    const Range R = my_range(a.m.n_slices);
+    stage_coarse(a.coarse, sh);
+    const Tab<float> tab = stage_tables<float>(a.m, a.m.val32, R, a.cache_cap, a.meta_slots, dsm);
+    Ring ring{};
+    if constexpr (STREAM) ring = make_ring(a, R, tab.meta, dsm, sh, false);
+    auto bail = [&]() {
+        if constexpr (STREAM)
+            if (threadIdx.x == 0) ring_drain(ring, a.budget_ns);
+        record_abort(a);
+    };
+    const int n = a.m.n;
+    const int ref = a.prm->ref;
+    const float pin32 = a.prm->pin32;
+    const int K = a.coarse->K;
+    const int rc = a.coarse->ref_comp;
+    const int nx = a.coarse->n_cross;
+    float *__restrict__ E = a.E;
+    const float *__restrict__ dinv = a.dinv32;
+
+    // prologue: x0, e = 0, ||b||
+    double vb[1] = {0.0};
+    for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
+        const int i = s * kSlice + R.lane;
+        if (i < n) {
+            a.x64[i] = a.use_x0 ? a.p_user[a.iperm[i]] : 0.0;
+            E[i] = 0.0f;
+            const double bi = a.b[i];
+            vb[0] += bi * bi;
+        }
+    }
+    block_sum_f64<1>(sh, vb);
+    double tb[1];
+    if (!grid_allreduce<1>(g, sh, vb, tb)) { bail(); return; }
+    if (threadIdx.x == 0) {
+        fs.bnorm = (tb[0] > 0.0) ? sqrt(tb[0]) : 1.0;
+        int ex;  // one power-of-two scale for the whole solve, as in the two-pass form
+        frexp(fs.bnorm / sqrt((double)n), &ex);
+        sh.ctl.alpha = ldexp(1.0, -ex);
+        sh.ctl.beta = ldexp(1.0, ex);
+        fs.rho_stop = (a.rtol * fs.bnorm * sh.ctl.alpha) * (a.rtol * fs.bnorm * sh.ctl.alpha);
+        fs.gam = 0.0;
+        fs.rho_max = 0.0;
+        fs.best_rel2 = 0.0;
+        fs.ps = 0.0;
+        fs.tdt = 0.0;
+        fs.stall = 0;
+        fs.last_upd = 0;
+    }
+    __syncthreads();
+    const double sc = sh.ctl.alpha, isc = sh.ctl.beta;
+
+    float4 *cur = a.Q0, *nxt = a.Q1;  // cur: the state the next pass reads
+    int iters = 0, updates = 0, status = GFM_OK;
+    double t[4];
+    double y_lane = 0.0;   // warp 0: Z^T r of the current state (lane k: component k)
+    double zk_lane = 0.0;  // warp 0: Z^T A p of the current state
+    if (!replace_fused<CH>(a, g, sh, R, cur, sc, isc, false, true, t, y_lane)) { bail(); return; }
+    ++updates;
+    if (threadIdx.x < 32) {
+        const double gam = fused_gamma(K, t[1], y_lane, sh);
+        if (threadIdx.x == 0) {
+            fs.best_rel2 = t[0] / (fs.bnorm * fs.bnorm);
+            fs.gam = gam;
+            fs.rho_max = t[3];
+            sh.ctl.action = (fs.best_rel2 <= a.rtol * a.rtol) ? kConverged : kGo;
+        }
+        fused_advance(K, gam, 0.0, 0.0, 0.0, 0.0, 0.0, y_lane, true, sh);
+    }
+    __syncthreads();
+    int action = sh.ctl.action;
+    if constexpr (STREAM)
+        if (threadIdx.x == 0) ring_prefetch(ring);
+    while (action != kConverged) {
+        const float al = sh.ctl.al, be = sh.ctl.be;
+        zero_bins(sh);
+        __syncthreads();
+        // the fused pass: the update of the last step and s' = A p' of this one
+        FF acc[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] = FF{0.f, 0.f};
+        if constexpr (STREAM) {
+            for (int r = 0; r < ring.nr; ++r) {
+                if (ring_wait(ring, a.budget_ns)) {
+                    const int sr0 = R.s0 + r * ring.stage_slices;
+                    const int sr1 = min(R.s1, sr0 + ring.stage_slices);
+                    const StageTab st = ring_stage(ring, r);
+                    for (int sb = sr0 + R.warp; sb < sr1; sb += US * R.nw)
+                        fused_group<CH, US>(st, sb, sr1, R, n, cur, nxt, E, dinv, al, be, ref, pin32, rc, K, sh, acc);
+                } else {
+                    sh.ring_fail = 1;
+                }
+                ++ring.used;
+                __syncthreads();  // stage consumed: it may be refilled
+                if (sh.ring_fail) break;
+                if (threadIdx.x == 0 && r + ring.n_stages < ring.nr) ring_issue(ring, r + ring.n_stages);
+            }
+            if (sh.ring_fail) {
+                if (threadIdx.x == 0) atomicCAS(a.err, 0, (int)GFM_ERR_TIMEOUT);
+                bail();
+                return;
+            }
+            if (threadIdx.x == 0) ring_prefetch(ring);
+        } else if (tab.full) {
+            const StageTab ft{tab.meta, tab.col, tab.val, tab.s0, tab.base0};
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
+                fused_group<CH, U>(ft, sb, R.s1, R, n, cur, nxt, E, dinv, al, be, ref, pin32, rc, K, sh, acc);
+        } else {
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += U * R.nw)
+                fused_group<CH, U>(tab, sb, R.s1, R, n, cur, nxt, E, dinv, al, be, ref, pin32, rc, K, sh, acc);
+        }
+        if (K > 0)  // Z^T (A p') from the faces between coarse regions (the pin's share is added above)
+            cross_sums<float>(a.cross, nx, K, sh.zbw32, [&](const CrossFace &cf) {
+                return cf.g32 * (fused_pnew(cur[cf.o], al, be, sh) - fused_pnew(cur[cf.v], al, be, sh));
+            });
+        double blk[5], tP[5 + kMaxCoarse];
+        block_sum_ff<5>(sh, acc, blk);
+        {
+            double b[5 + kMaxCoarse];
+            for (int k = 0; k < 5; ++k) b[k] = blk[k];
+            if (K > 0 && threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, rc, K, R.nw, sh.zb32);
+            for (int k = 0; k < kMaxCoarse; ++k) b[5 + k] = (K > 0) ? (double)sh.zb32[k] : 0.0;
+            // also the barrier after which the next pass gathers the new state
+            if (!grid_allreduce<5 + kMaxCoarse>(g, sh, b, tP, 5 + K)) { bail(); return; }
+        }
+        ++iters;
+        { float4 *tmp = cur; cur = nxt; nxt = tmp; }
+        if (threadIdx.x < 32) {
+            double zl = 0.0;
+#pragma unroll
+            for (int k = 0; k < kMaxCoarse; ++k)
+                if (k == R.lane && k < K) zl = tP[5 + k];
+            zk_lane = zl;
+            const double gam = fused_gamma(K, tP[1], y_lane, sh);
+            if (threadIdx.x == 0) {
+                const double ps = tP[0], rho = tP[4];
+                fs.gam = gam;
+                fs.ps = ps;
+                fs.tdt = tP[3];
+                if (rho > fs.rho_max) fs.rho_max = rho;
+                if (iters >= a.max_iters) {
+                    sh.ctl.action = kNotConverged;
+                } else if (!(ps > 0.0) || !isfinite(ps) || !(gam > 0.0)) {
+                    sh.ctl.action = kRestart;  // breakdown of the FP32 recurrence
+                } else if (rho <= 1e-2 * fs.rho_max || rho <= fs.rho_stop || iters - fs.last_upd >= 1000) {
+                    // replacement when the FP32 residual fell a decade, claims
+                    // convergence, or has not fallen a decade for 1000 iterations
+                    sh.ctl.action = kUpdate;
+                    fs.last_upd = iters;
+                } else {
+                    sh.ctl.action = kGo;
+                }
+            }
+            __syncwarp();
+            if (sh.ctl.action == kGo)
+                fused_advance(K, gam, tP[0], tP[1], tP[2], tP[3], zk_lane, y_lane, false, sh);
+        }
+        __syncthreads();
+        action = sh.ctl.action;
+        if (action == kGo) continue;
+        // fold e into x (FP64) and replace r by the true residual; the
+        // direction is kept, or cleared on a restart
+        const bool restart = action == kRestart;
+        if (!replace_fused<CH>(a, g, sh, R, cur, sc, isc, true, restart, t, y_lane)) { bail(); return; }
+        ++updates;
+        if (threadIdx.x < 32) {
+            const double gam = fused_gamma(K, t[1], y_lane, sh);
+            if (threadIdx.x == 0) {
+                const double rel2 = t[0] / (fs.bnorm * fs.bnorm);
+                if (rel2 <= a.rtol * a.rtol) {
+                    sh.ctl.action = kConverged;
+                } else if (restart) {
+                    sh.ctl.action = (++fs.stall > 3) ? kBreakdown : kGo;
+                } else if (sh.ctl.action != kNotConverged) {
+                    if (rel2 < 0.25 * fs.best_rel2) {
+                        fs.best_rel2 = rel2;
+                        fs.stall = 0;
+                    } else {
+                        ++fs.stall;
+                    }
+                    if (fs.stall > 8 || updates > a.max_refine + 1 + (int)(2.0 * log10(1.0 / a.rtol)))
+                        sh.ctl.action = kNotConverged;
+                    else
+                        sh.ctl.action = kGo;
+                }
+                if (sh.ctl.action == kGo) {
+                    fs.gam = gam;
+                    fs.rho_max = t[3];
+                }
+            }
+            __syncwarp();
+            if (sh.ctl.action == kGo) {
+                // the kept direction's p.s and t.D t are unchanged; t.D q is the new one
+                const bool ok = restart || (fs.ps > 0.0 && gam > 0.0);
+                fused_advance(K, gam, fs.ps, t[1], t[2], fs.tdt, zk_lane, y_lane, !ok, sh);
+            }
+        }
+        __syncthreads();
+        action = sh.ctl.action;
+        if (action == kBreakdown) { status = GFM_ERR_BREAKDOWN; break; }
+        if (action == kNotConverged) { status = GFM_ERR_NOT_CONVERGED; break; }
+    }
+    if constexpr (STREAM)
+        if (threadIdx.x == 0) ring_drain(ring, a.budget_ns);
+    finish<CH>(a, g, sh, R, iters, updates, status, fs.bnorm);
+}
+
+// ---------------------------------------------------------------------------
 // Batched mixed-precision solve: many independent tanks in one persistent
 // launch.  Every CTA works on one tank at a time; per-tank scalars live in
 // shared memory and every CTA computes ALL tanks' sums and decisions from the
@@ -2554,10 +3004,15 @@ const void *batched_kernel(int max_width, bool streamed, bool compact)
 // and, for the mixed solver, by how the operator pass reads the tables
 // (streamed through shared-memory stages -- in full or compact form -- or
 // cached / read in place).
-const void *solver_kernel(Mode m, int max_width, int threads, bool streamed, bool compact)
+const void *solver_kernel(Mode m, int max_width, int threads, bool streamed, bool compact, bool fused)
 {
     (void)threads;
     const bool ct = streamed && compact;
+    if (m == Mode::MIXED && fused && !ct) {
+        if (max_width <= 4) return streamed ? (const void *)k_solve_fused<4, true> : (const void *)k_solve_fused<4, false>;
+        if (streamed && max_width <= 6) return (const void *)k_solve_fused<6, true>;
+        return streamed ? (const void *)k_solve_fused<8, true> : (const void *)k_solve_fused<8, false>;
+    }
     if (max_width <= 4) {
         if (m == Mode::FP64) return (const void *)k_solve_fp64<4>;
         if (ct) return (const void *)k_solve_mixed<4, true, true>;

@@ -36,27 +36,32 @@ def test_traffic_record_only_while_the_source_is_unchanged(tmp_path, monkeypatch
     source = b"// solver source as measured\n"
     sha = hashlib.sha256(source).hexdigest()[:16]
     _fake_tree(tmp_path, source, {
-        "tank2d": {"source_sha": sha, "dram_bytes_per_launch": 1.0e8},
-        "box3d": {"source_sha": "0" * 16, "dram_bytes_per_launch": 4.0e11},
+        "tank2d": {"source_sha": sha, "kernel": "void k_solve_fused<4, 0>(SolveArgs)", "dram_bytes_per_launch": 1.0e8},
+        "box3d": {"source_sha": "0" * 16, "kernel": "void k_solve_mixed<6, 1, 0>(SolveArgs)",
+                  "dram_bytes_per_launch": 4.0e11},
     })
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    rec, got = bench._traffic_record("tank2d")
+    rec, got = bench._traffic_record("tank2d", "k_solve_fused")
     assert got == sha and rec["dram_bytes_per_launch"] == 1.0e8
+    # a capture of another kernel (the other iteration form): not reported
+    rec, _ = bench._traffic_record("tank2d", "k_solve_mixed")
+    assert rec is None
     # measured on another source: not reported
-    rec, _ = bench._traffic_record("box3d")
+    rec, _ = bench._traffic_record("box3d", "k_solve_mixed")
     assert rec is None
     # no record at all
-    rec, _ = bench._traffic_record("batch64")
+    rec, _ = bench._traffic_record("batch64", "k_solve_batched")
     assert rec is None
     # the source changes after the capture: the record stops counting
     (tmp_path / "paper_1804_01130_gb300" / "csrc" / "gfm_solve.cu").write_bytes(source + b"// edited\n")
-    rec, _ = bench._traffic_record("tank2d")
+    rec, _ = bench._traffic_record("tank2d", "k_solve_fused")
     assert rec is None
 
 
 def test_committed_traffic_records_name_their_kernels():
     with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
         recs = json.load(fh)
-    for workload, kernel in (("tank2d", "k_solve_mixed"), ("box3d", "k_solve_mixed"), ("batch64", "k_solve_batched")):
+    for workload, kernels in (("tank2d", ("k_solve_mixed", "k_solve_fused")), ("box3d", ("k_solve_mixed", "k_solve_fused")),
+                              ("batch64", ("k_solve_batched",))):
         r = recs[workload]
-        assert kernel in r["kernel"] and r["dram_bytes_per_launch"] > 0 and len(r["source_sha"]) == 16
+        assert any(k in r["kernel"] for k in kernels) and r["dram_bytes_per_launch"] > 0 and len(r["source_sha"]) == 16

@@ -1,8 +1,9 @@
 """GPU parity at the benchmark sizes, in the launch configuration bench.py
 times (default launch shape, the workloads' renumbering and tolerances):
 
-- the 1024x512 wave tank (524 288 cells): full arrays against the oracle,
-  and the GFM pressure gradient and velocity reconstruction;
+- the 1024x512 wave tank (524 288 cells): full arrays against the oracle
+  (both forms of the mixed solve), and the GFM pressure gradient and
+  velocity reconstruction;
 - the 256x128x128 green-water box (4.2M cells, permuted), whose tables are
   streamed through shared-memory stages: full assembly, the true residual
   of the solution through the oracle's own matrix, the FP64 and mixed
@@ -91,6 +92,14 @@ def test_tank2d_1024x512_full_size():
     pmn = pm.cpu().numpy()
     assert _true_rel(sy, pmn) <= 1.05e-10
     assert _rel(pmn, p_ref) <= 1e-6
+    # the fused form (one all-reduce per iteration), the form the bench's
+    # autotuner may pick for this mesh
+    s.set_tuning(form=2)
+    pf, _, inf = s.solve(mode="mixed", rtol=1e-10, inner_rtol=1e-4)
+    assert inf.status == 0
+    pfn = pf.cpu().numpy()
+    assert _true_rel(sy, pfn) <= 1.05e-10
+    assert _rel(pfn, p_ref) <= 1e-6
 
 
 def test_box3d_256x128x128_full_size():
@@ -108,6 +117,13 @@ def test_box3d_256x128x128_full_size():
     pm, _, im = s.solve(mode="mixed", rtol=1e-10)
     assert im.status == 0
     assert _rel(pm.cpu().numpy(), p_ref) <= 1e-6
+    # the fused form with streamed tables
+    s.set_tuning(form=2)
+    pf, _, inf = s.solve(mode="mixed", rtol=1e-10)
+    assert inf.status == 0
+    assert _true_rel(sy, pf.cpu().numpy()) <= 1.05e-10
+    assert _rel(pf.cpu().numpy(), p_ref) <= 1e-6
+    s.set_tuning(form=1)
     p64, _, i64 = s.solve(mode="fp64", rtol=1e-12)
     assert i64.status == 0
     assert _rel(p64.cpu().numpy(), p_ref) <= 1e-9
