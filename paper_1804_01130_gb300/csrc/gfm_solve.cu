@@ -468,7 +468,10 @@ __device__ __forceinline__ void ring_issue(Ring &g, int r)
     float *val = reinterpret_cast<float *>(col + g.cap);
     mbar_arrive_expect_tx(bar, 2u * bytes);
     if (bytes != 0u) {
-        // the tables stream through once per pass: evict-first in L2
+        // the tables stream through once per pass: evict-first in L2 (keeping
+        // a share of them resident with evict-last instead was slower on the
+        // 256x128x128 box: 108.5 ms with none, 112.5 with a quarter, 115.5
+        // with half, as those lines crowd out the gathered vectors)
         const unsigned long long pol = l2_evict_first();
         bulk_load(col, g.gcol + b, bytes, bar, pol);
         bulk_load(val, g.gval + b, bytes, bar, pol);
@@ -2031,15 +2034,16 @@ __global__ void __launch_bounds__(512, 1) k_solve_fused(SolveArgs a)
             sh.ctl.action = (fs.best_rel2 <= a.rtol * a.rtol) ? kConverged : kGo;
         }
         fused_advance(K, gam, 0.0, 0.0, 0.0, 0.0, 0.0, y_lane, true, sh);
+        zero_bins(sh);
     }
     __syncthreads();
     int action = sh.ctl.action;
     if constexpr (STREAM)
         if (threadIdx.x == 0) ring_prefetch(ring);
     while (action != kConverged) {
+        // al, be, sh.cz and the cleared coarse bins were published by warp 0
+        // before the CTA barrier that ended the last scalar step
         const float al = sh.ctl.al, be = sh.ctl.be;
-        zero_bins(sh);
-        __syncthreads();
         // the fused pass: the update of the last step and s' = A p' of this one
         FF acc[5];
 #pragma unroll
@@ -2091,6 +2095,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_fused(SolveArgs a)
         ++iters;
         { float4 *tmp = cur; cur = nxt; nxt = tmp; }
         if (threadIdx.x < 32) {
+            zero_bins(sh);  // this pass's bins were read before the all-reduce
             double zl = 0.0;
 #pragma unroll
             for (int k = 0; k < kMaxCoarse; ++k)
@@ -2204,6 +2209,7 @@ struct TankState {
     double *red;  // dynamic shared memory: [kBatchNR][G] CTA partials
     unsigned ring_used;  // thread 0's count of consumed stages after a drain
     double Einv[kTankCoarse * kTankCoarse][kMaxTanks];
+    float Einv32[kTankCoarse * kTankCoarse][kMaxTanks];  // the same in FP32 (the FP32 iterations' correction)
     double y[kTankCoarse][kMaxTanks];
     float c32[kTankCoarse][kMaxTanks];
     int act[kMaxTanks];   // kGo while iterating, else kConverged / kNotConverged / kBreakdown
@@ -2281,6 +2287,26 @@ __device__ __forceinline__ void list_wide(TankState &ts, int T)
 }
 
 // One lane, one tank: c = E^{-1} y into ts.c32 (K <= 2); returns y.c.
+// The FP32 iterations' form: c = E^{-1} y from the FP32 inverse and the
+// rounded y (the vectors apply c in FP32; a chain of FP64 multiply-adds per
+// tank costs far more on GB300's FP64 pipe).
+__device__ __forceinline__ void tank_coarse_solve32(TankState &ts, int t)
+{
+    const int K = ts.K[t];
+    float yf[kTankCoarse];
+#pragma unroll
+    for (int j = 0; j < kTankCoarse; ++j) yf[j] = (j < K) ? (float)ts.y[j][t] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < kTankCoarse; ++i) {
+        if (i >= K) break;
+        float c = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kTankCoarse; ++j)
+            if (j < K) c = fmaf(ts.Einv32[i * kTankCoarse + j][t], yf[j], c);
+        ts.c32[i][t] = c;
+    }
+}
+
 __device__ __forceinline__ double tank_coarse_solve(TankState &ts, int t)
 {
     const int K = ts.K[t];
@@ -2609,6 +2635,30 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             }
         }
     };
+    // warp 0 counts the tanks still iterating; when some have finished,
+    // every CTA re-plans the tank->CTA table and takes its new range.  Ends
+    // with a CTA barrier.  (Always true: kept for the bail-out pattern.)
+    auto replan_if_finished = [&]() -> bool {
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int nact = 0;
+            for (int t0 = 0; t0 < T; t0 += 32)
+                nact += __popc(__ballot_sync(0xffffffffu, t0 + (int)threadIdx.x < T && ts.act[t0 + threadIdx.x] == kGo));
+            if (threadIdx.x == 0) {
+                ts.any_active = nact > 0;
+                sh.flag = (nact > 0 && nact < ts.n_active);  // tanks finished: re-plan
+                if (sh.flag) ts.n_active = nact;
+            }
+            __syncwarp();
+            if (sh.flag) batch_rebalance(ts, T, (int)gridDim.x, false);
+        }
+        __syncthreads();
+        if (sh.flag) {
+            take_assignment(true);
+            __syncthreads();
+        }
+        return true;
+    };
     float *__restrict__ E = a.E;
     float *__restrict__ R32 = a.R32;
     float *__restrict__ S32 = a.S32;
@@ -2653,7 +2703,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
             ts.rc[t] = tc.ref_comp;
             ts.x0[t] = tc.x0;
             ts.x1[t] = tc.x1;
-            for (int q = 0; q < kTankCoarse * kTankCoarse; ++q) ts.Einv[q][t] = tc.Einv[q];
+            for (int q = 0; q < kTankCoarse * kTankCoarse; ++q) {
+                ts.Einv[q][t] = tc.Einv[q];
+                ts.Einv32[q][t] = (float)tc.Einv[q];
+            }
             for (int k = 0; k < kTankCoarse; ++k) {
                 ts.y[k][t] = 0.0;
                 ts.c32[k][t] = 0.0f;
@@ -2686,15 +2739,17 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         ts.n_active = T;  // re-plan as soon as any tank is done
         if constexpr (STREAM) ring_prefetch(ring);
     }
-    __syncthreads();
+    if (threadIdx.x < 32) zero_bins(sh);
+    // tanks that the start already solves give their CTAs away at once
+    if (!replan_if_finished()) { bail(); return; }
     while (ts.any_active) {
         const bool work = ts.act[tank] == kGo && ts.wait[tank] == 0;
         const float be = ts.be[tank];
         // pass A: p = u + beta p (own and, redundantly, neighbours), s = A p, p.s,
         // and the tank's Z^T (A p) from its faces between coarse regions
         const int Kt = ts.K[tank];
-        zero_bins(sh);
-        __syncthreads();
+        // the coarse bins were cleared by warp 0 in the last alpha step (or
+        // before the loop), ahead of a CTA barrier
         FF accA[1] = {{0.f, 0.f}};
         if constexpr (STREAM) {
             // every stage is waited for, so the ring stays in step even when
@@ -2759,15 +2814,19 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         for (int k = 0; k < kTankCoarse; ++k) blkA[1 + k] = (work && k < Kt) ? (double)sh.zb32[k] : 0.0;
         if (!batch_allreduce<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { bail(); return; }
         if (threadIdx.x < 32) {
+            zero_bins(sh);  // this pass's bins were read before the all-reduce
             for (int t = threadIdx.x; t < T; t += 32) {
                 if (ts.act[t] != kGo || ts.wait[t]) continue;
                 const double ps = ts.tot[0][t];
                 const bool ok = ps > 0.0 && isfinite(ps) && ts.gam[t] > 0.0;
-                ts.al[t] = ok ? (float)(ts.gam[t] / ps) : 0.0f;
+                // alpha in FP32, the vectors' precision (an FP64 divide per tank
+                // costs more than the whole step on GB300's FP64 pipe)
+                const float al = ok ? (float)ts.gam[t] / (float)ps : 0.0f;
+                ts.al[t] = al;
                 ts.flag[t] = ok ? 0 : kRestart;
-                if (ok && ts.K[t] > 0) {  // y -= alpha Z^T A p, c = E^{-1} y
-                    for (int k = 0; k < ts.K[t]; ++k) ts.y[k][t] = fma(-(double)ts.al[t], ts.tot[1 + k][t], ts.y[k][t]);
-                    tank_coarse_solve(ts, t);
+                if (ok && ts.K[t] > 0) {  // y -= alpha Z^T A p (FP64), c = E^{-1} y (FP32)
+                    for (int k = 0; k < ts.K[t]; ++k) ts.y[k][t] = fma(-(double)al, ts.tot[1 + k][t], ts.y[k][t]);
+                    tank_coarse_solve32(ts, t);
                 }
             }
         }
@@ -2777,18 +2836,20 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         FF accB[2] = {{0.f, 0.f}, {0.f, 0.f}};
         if (work && ts.flag[tank] == 0) {
             for (int sb = R.s0 + R.warp; sb < R.s1; sb += UB * R.nw) {
-                int ii[UB];
+                int ii[UB], cm[UB];
                 bool act[UB];
                 float pi[UB], si[UB], ri[UB], ei[UB], di[UB];
 #pragma unroll
                 for (int u = 0; u < UB; ++u) {
                     ii[u] = (sb + u * R.nw) * kSlice + R.lane;
                     act[u] = sb + u * R.nw < R.s1 && ii[u] < cend;
+                    // every load of the group in flight together
                     pi[u] = act[u] ? __ldcs(P32 + ii[u]) : 0.f;
                     si[u] = act[u] ? __ldcs(S32 + ii[u]) : 0.f;
                     ri[u] = act[u] ? __ldcs(R32 + ii[u]) : 0.f;
                     ei[u] = act[u] ? __ldcs(E + ii[u]) : 0.f;
                     di[u] = act[u] ? __ldcs(dinv + ii[u]) : 0.f;
+                    cm[u] = (act[u] && Kt > 0) ? (int)a.comp[ii[u]] : -1;
                 }
 #pragma unroll
                 for (int u = 0; u < UB; ++u) {
@@ -2797,10 +2858,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                         const float rn = fmaf(-al, si[u], ri[u]);
                         __stcs(R32 + ii[u], rn);
                         float un = rn * di[u];
-                        if (Kt > 0) {
-                            const int cm = a.comp[ii[u]];
-                            if (cm >= 0) un += ts.c32[cm][tank];
-                        }
+                        if (cm[u] >= 0) un += ts.c32[cm[u]][tank];
                         nxt[ii[u]] = make_float2(un, pi[u]);
                         ff_add(accB[0], rn * un);
                         ff_add(accB[1], rn * rn);
@@ -2862,7 +2920,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                         if (it - ts.last_rep[t] < 2 * kReplaceRound) ts.wait[t] = 1;
                     }
                     if (ts.wait[t] == 0) {
-                        ts.be[t] = (float)(gam / ts.gam_prev[t]);
+                        ts.be[t] = (float)gam / (float)ts.gam_prev[t];
                         going = true;
                     }
                 }
@@ -2913,23 +2971,12 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                     ts.gam[t] = ts.tot[1][t];
                     ts.rho_max[t] = ts.tot[2][t];
                     ts.be[t] = (f == kRestart || !(ts.gam_prev[t] > 0.0)) ? 0.0f
-                                                                           : (float)(ts.gam[t] / ts.gam_prev[t]);
+                                                                           : (float)ts.gam[t] / (float)ts.gam_prev[t];
                 }
             }
-            __syncthreads();
+            // tanks only finish in a replacement round: re-plan here
+            if (!replan_if_finished()) { bail(); return; }
         }
-        if (threadIdx.x == 0) {
-            int nact = 0;
-            for (int t = 0; t < T; ++t) nact += ts.act[t] == kGo;
-            ts.any_active = nact > 0;
-            sh.flag = (nact > 0 && nact < ts.n_active);  // tanks finished: re-plan
-            if (sh.flag) ts.n_active = nact;
-        }
-        __syncwarp();
-        if (threadIdx.x < 32 && sh.flag) batch_rebalance(ts, T, (int)gridDim.x, false);
-        __syncthreads();
-        if (sh.flag) take_assignment(true);
-        __syncthreads();
     }
     // every tank gets CTAs again for the final residuals
     if (threadIdx.x < 32) batch_rebalance(ts, T, (int)gridDim.x, true);
