@@ -638,6 +638,43 @@ __device__ __forceinline__ double apply64_diff(const Sell &m, Row rw, int lane, 
     return acc;
 }
 
+// The difference form for UR rows at once (slices s[u], inactive rows give
+// pin_i x_i): every row's table and neighbour loads are in flight together,
+// so UR rows cost the dependent round trips of one.
+template <int CH, int UR>
+__device__ __forceinline__ void apply64_diff_multi(const Sell &m, const Row (&rw)[UR], int lane, const double *x,
+                                                   const double (&xi)[UR], const double (&pin)[UR],
+                                                   double (&acc)[UR])
+{
+    int wmax = 0;
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+        acc[u] = pin[u] * xi[u];
+        wmax = max(wmax, rw[u].w);
+    }
+    for (int k0 = 0; k0 < wmax; k0 += CH) {
+        int j[UR][CH];
+        double gm[UR][CH], xj[UR][CH];
+#pragma unroll
+        for (int u = 0; u < UR; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const bool ok = k0 + c < rw[u].w;
+                const int slot = rw[u].base + (k0 + c) * kSlice + lane;
+                j[u][c] = ok ? __ldg(m.col + slot) : 0;
+                gm[u][c] = ok ? __ldg(m.val64 + slot) : 0.0;
+            }
+#pragma unroll
+        for (int u = 0; u < UR; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) xj[u][c] = (k0 + c < rw[u].w) ? x[j[u][c]] : xi[u];
+#pragma unroll
+        for (int u = 0; u < UR; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) acc[u] = fma(gm[u][c], xi[u] - xj[u][c], acc[u]);
+    }
+}
+
 // (A x)_i in FP64, diagonal form: diag_i x_i - sum_f gamma_f x_j.
 template <int CH>
 __device__ __forceinline__ double apply64_diag(const Sell &m, Row rw, int lane, const double *x, double xi,
@@ -2335,11 +2372,25 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
     double *x = a.x64;
     if (fold) {
         if (work) {
-            for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-                const int i = s * kSlice + R.lane;
-                if (i < cend) {
-                    x[i] = fma((double)a.E[i], isc, x[i]);
-                    a.E[i] = 0.0f;
+            // four slices per warp at a time, their loads in flight together
+            constexpr int UF = 4;
+            for (int sb = R.s0 + R.warp; sb < R.s1; sb += UF * R.nw) {
+                float e[UF];
+                double xv[UF];
+#pragma unroll
+                for (int u = 0; u < UF; ++u) {
+                    const int i = (sb + u * R.nw) * kSlice + R.lane;
+                    const bool act = sb + u * R.nw < R.s1 && i < cend;
+                    e[u] = act ? a.E[i] : 0.0f;
+                    xv[u] = act ? x[i] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < UF; ++u) {
+                    const int i = (sb + u * R.nw) * kSlice + R.lane;
+                    if (sb + u * R.nw < R.s1 && i < cend) {
+                        x[i] = fma((double)e[u], isc, xv[u]);
+                        a.E[i] = 0.0f;
+                    }
                 }
             }
         }
@@ -2348,22 +2399,43 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
     double vr[1] = {0.0};
     FF acc[2 + kTankCoarse] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (work) {
-        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-            const int i = s * kSlice + R.lane;
-            if (i < cend) {
-                const double xi = x[i];
-                const double ri = a.b[i] - apply64_diff<CH>(a.m, row_of(a.m, s), R.lane, x, xi, i == ref ? pin64 : 0.0);
+        // two slices per warp at a time: the residual pass is a chain of
+        // dependent loads per row (slice table, slots, neighbours)
+        constexpr int UR = 2;
+        for (int sb = R.s0 + R.warp; sb < R.s1; sb += UR * R.nw) {
+            int ii[UR], cm[UR];
+            bool act[UR];
+            Row rw[UR];
+            double xi[UR], bi[UR], pin[UR], ax[UR];
+            float di[UR];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int s = sb + u * R.nw;
+                ii[u] = s * kSlice + R.lane;
+                act[u] = s < R.s1 && ii[u] < cend;
+                rw[u] = act[u] ? row_of(a.m, s) : Row{0, 0};
+                xi[u] = act[u] ? x[ii[u]] : 0.0;
+                bi[u] = act[u] ? a.b[ii[u]] : 0.0;
+                di[u] = act[u] ? a.dinv32[ii[u]] : 0.0f;
+                cm[u] = act[u] ? (int)a.comp[ii[u]] : -1;
+                pin[u] = (act[u] && ii[u] == ref) ? pin64 : 0.0;
+            }
+            apply64_diff_multi<CH, UR>(a.m, rw, R.lane, x, xi, pin, ax);
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                if (!act[u]) continue;
+                const int i = ii[u];
+                const double ri = bi[u] - ax[u];
                 vr[0] = fma(ri, ri, vr[0]);
                 const float r32 = (float)(ri * sc);
-                const float u = r32 * a.dinv32[i];
+                const float uu = r32 * di[u];
                 a.R32[i] = r32;
-                if (zero_p) up[i] = make_float2(u, 0.0f);
-                else up[i].x = u;
-                ff_add(acc[0], r32 * u);
+                if (zero_p) up[i] = make_float2(uu, 0.0f);
+                else up[i].x = uu;
+                ff_add(acc[0], r32 * uu);
                 ff_add(acc[1], r32 * r32);
-                const int cm = a.comp[i];
 #pragma unroll
-                for (int k = 0; k < kTankCoarse; ++k) ff_add(acc[2 + k], (cm == k) ? r32 : 0.0f);
+                for (int k = 0; k < kTankCoarse; ++k) ff_add(acc[2 + k], (cm[u] == k) ? r32 : 0.0f);
             }
         }
     }
