@@ -229,9 +229,6 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
             max_slots = std::max(max_slots, h->ht.slice_ptr[(size_t)s1] - h->ht.slice_ptr[(size_t)s0]);
         }
     }
-    // the batched solve keeps one all-reduce's CTA partials ahead of its tables
-    const long long red_bytes = h->batched ? gfm::batch_red_bytes(grid) : 0;
-    budget -= red_bytes;
     const int meta_slots = (max_nsl + 1) & ~1;
     const long long meta_bytes = (long long)meta_slots * 8;
     const long long slot_bytes = 4 + (mode == gfm::Mode::FP64 ? 8 : 4);
@@ -265,7 +262,7 @@ gfm_status plan_launch(gfm_ctx *h, gfm::Mode mode, LaunchPlan *lp)
         }
         if (n_stages) cap = 0;
     }
-    const size_t dyn = (size_t)(red_bytes + meta_bytes +
+    const size_t dyn = (size_t)(meta_bytes +
                                 (n_stages ? (long long)n_stages * stage_cap * sbytes + dict_bytes : cap * slot_bytes));
     if (n_stages)
         k = h->batched ? gfm::batched_kernel(h->ht.max_width, true, ct)

@@ -47,9 +47,6 @@ constexpr int kTankCoarse = 2;
 constexpr int kMaxReduce = 16;  // most values one grid all-reduce of a single mesh sums
 constexpr int kBatchNR = 3 + kTankCoarse;  // most values one batched all-reduce sums
 constexpr int kLaneSum = 8;                // tanks with more CTAs are summed by a warp
-// bytes of dynamic shared memory ahead of the batched solve's tables: the
-// CTA partials of one all-reduce, [kBatchNR][grid] doubles
-__host__ __device__ constexpr int batch_red_bytes(int grid) { return (kBatchNR * grid * 8 + 15) & ~15; }
 struct TankCoarse {
     int32_t K, ref_comp, x0, x1;
     int32_t roots[kTankCoarse], sizes[kTankCoarse];

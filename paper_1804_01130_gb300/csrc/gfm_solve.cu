@@ -2243,7 +2243,6 @@ struct TankState {
     // tanks with more than kLaneSum CTAs, whose partials a whole warp sums
     int wide[kMaxTanks];
     int n_wide;
-    double *red;  // dynamic shared memory: [kBatchNR][G] CTA partials
     unsigned ring_used;  // thread 0's count of consumed stages after a drain
     double Einv[kTankCoarse * kTankCoarse][kMaxTanks];
     float Einv32[kTankCoarse * kTankCoarse][kMaxTanks];  // the same in FP32 (the FP32 iterations' correction)
@@ -2261,18 +2260,18 @@ struct TankState {
     int round_age;  // iterations since the last replacement round
 };
 
-// Per-tank all-reduce.  Every CTA writes its partials, and after the grid
-// barrier copies all of them (one coalesced read) into shared memory; then
-// value k of tank t is the sum over the tank's CTAs in CTA order, by one
-// thread when the tank has at most kLaneSum CTAs, else by one warp (lane l
-// takes CTAs l, l + 32, ..., then a fixed butterfly).  Which rule a tank gets
+// Per-tank all-reduce.  Every CTA writes its partials; after the grid
+// barrier value k of tank t is the sum over the tank's CTAs in CTA order, by
+// one thread when the tank has at most kLaneSum CTAs (its loads all in
+// flight at once), else by one warp (lane l takes CTAs l, l + 32, ..., then
+// a fixed butterfly), reading the partials straight from L2.  Which rule a tank gets
 // depends only on the CTA table, which every CTA holds, so every CTA gets the
 // same bits.
 template <int NR>
 __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &ts, const BatchArgs &bt,
                                                 const double (&blk)[NR])
 {
-    static_assert(NR <= kBatchNR, "batched reduction buffer too small");
+    static_assert(NR <= kBatchNR && kBatchNR <= kMaxNR, "more values than a batched all-reduce carries");
     int e = 0;
     __syncthreads();
     g.epoch += 1u;
@@ -2286,16 +2285,19 @@ __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &
     __syncthreads();
     if (sh.flag != 0) return false;
     const int G = g.G, T = bt.T;
-    double *red = ts.red;
     const double *src = g.partials + (size_t)g.parity * kMaxNR * G;
-    for (int i = threadIdx.x; i < NR * G; i += blockDim.x) red[i] = __ldcg(src + i);
-    __syncthreads();
     for (int i = threadIdx.x; i < NR * T; i += blockDim.x) {
         const int k = i / T, t = i - k * T;
         const int2 r = ts.tcta[t];
-        if (r.y - r.x > kLaneSum) continue;
+        const int nc = r.y - r.x;
+        if (nc > kLaneSum) continue;
+        double v[kLaneSum];
+#pragma unroll
+        for (int q = 0; q < kLaneSum; ++q) v[q] = (q < nc) ? __ldcg(src + k * G + r.x + q) : 0.0;
         double acc = 0.0;
-        for (int c = r.x; c < r.y; ++c) acc += red[k * G + c];
+#pragma unroll
+        for (int q = 0; q < kLaneSum; ++q)
+            if (q < nc) acc += v[q];
         ts.tot[k][t] = acc;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -2303,7 +2305,7 @@ __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &
         const int k = i / ts.n_wide, t = ts.wide[i - k * ts.n_wide];
         const int2 r = ts.tcta[t];
         double acc = 0.0;
-        for (int c = r.x + lane; c < r.y; c += 32) acc += red[k * G + c];
+        for (int c = r.x + lane; c < r.y; c += 32) acc += __ldcg(src + k * G + c);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) ts.tot[k][t] = acc;
@@ -2461,9 +2463,22 @@ __device__ bool batch_replace(const SolveArgs &a, const BatchArgs &bt, Grid &g, 
     if (sh.flag == 0) return true;  // the same in every CTA
     __syncthreads();
     if (work && ts.K[tank] > 0) {
-        for (int s = R.s0 + R.warp; s < R.s1; s += R.nw) {
-            const int i = s * kSlice + R.lane;
-            if (i < cend && a.comp[i] >= 0) up[i].x += ts.c32[a.comp[i]][tank];
+        constexpr int UF = 4;  // four slices per warp at a time, their loads in flight together
+        for (int sb = R.s0 + R.warp; sb < R.s1; sb += UF * R.nw) {
+            int cm[UF];
+            float ux[UF];
+#pragma unroll
+            for (int u = 0; u < UF; ++u) {
+                const int i = (sb + u * R.nw) * kSlice + R.lane;
+                const bool act = sb + u * R.nw < R.s1 && i < cend;
+                cm[u] = act ? (int)a.comp[i] : -1;
+                ux[u] = act ? up[i].x : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < UF; ++u) {
+                const int i = (sb + u * R.nw) * kSlice + R.lane;
+                if (cm[u] >= 0) up[i].x = ux[u] + ts.c32[cm[u]][tank];
+            }
         }
     }
     return grid_sync(g, sh);  // u complete before it is gathered
@@ -2628,8 +2643,8 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
     extern __shared__ __align__(16) unsigned char dsm[];
     Grid g{a.bar, a.err, a.partials, a.budget_ns, 0u, (int)gridDim.x, 0};
     const int T = bt.T;
-    // dynamic shared memory: the reduction buffer, then the staged tables
-    unsigned char *tdsm = dsm + batch_red_bytes((int)gridDim.x);
+    // dynamic shared memory: the staged tables
+    unsigned char *tdsm = dsm;
     // this CTA's tank and slices: from the planned table at first, from the
     // re-planned one (ts.tcta) once tanks have finished
     const int4 me = bt.cta[blockIdx.x];
@@ -2654,10 +2669,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
         }
     }
     __syncwarp();  // thread 0 reads what the other lanes of warp 0 wrote
-    if (threadIdx.x == 0) {
-        ts.red = reinterpret_cast<double *>(dsm);
-        list_wide(ts, T);
-    }
+    if (threadIdx.x == 0) list_wide(ts, T);
     BTab tab = stage_btab(a.m, R, STREAM ? 0 : a.cache_cap, a.meta_slots, tdsm);  // ends with a block barrier
     // streamed tables: the ring follows the CTA's range; a range longer than
     // the metadata area (the host sizes it for every re-plan) is an error
