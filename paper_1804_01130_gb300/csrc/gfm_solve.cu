@@ -292,6 +292,83 @@ __device__ __forceinline__ void block_sum_ff(Shared &sh, FF (&v)[NR], double (&o
     }
 }
 
+// The same, leaving thread 0 the double-float pair (hi, lo) of each sum.
+template <int NR>
+__device__ __forceinline__ void block_sum_ff2(Shared &sh, FF (&v)[NR], float2 (&out)[NR])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = ff_shfl_tree(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) sh.warp_ff[warp][k] = make_float2(v[k].hi, v[k].lo);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const float2 t = (lane < nw) ? sh.warp_ff[lane][k] : make_float2(0.f, 0.f);
+            const FF r = ff_shfl_tree(FF{t.x, t.y});
+            out[k] = make_float2(r.hi, r.lo);
+        }
+    }
+}
+
+// Deterministic all-reduce of double-float partials (thread 0's blk, one
+// (hi, lo) pair per value) across the grid, in double-float arithmetic: the
+// FP32 iterations' sums are double-float already, and on GB300 a warp's FP64
+// add costs the FP64 pipe as much as a dozen FP32 instructions, so summing
+// 152 partials per value in FP64 in up to 13 warps at once queued on that pipe.
+// Same order and structure as grid_allreduce; each sum ends as hi + lo in FP64.
+template <int NR>
+__device__ __forceinline__ bool grid_allreduce_ff(Grid &g, Shared &sh, const float2 (&blk)[NR], double (&out)[NR],
+                                                  int nr = NR)
+{
+    static_assert(NR <= kMaxNR, "grid reduction buffer too small");
+    int e = 0;
+    __syncthreads();
+    g.epoch += 1u;
+    float2 *pp = reinterpret_cast<float2 *>(g.partials);  // one 8-byte slot per value and CTA, as for doubles
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+            if (k < nr) pp[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
+        const bool ok = grid_arrive_wait(g);
+        e = ok ? ld_volatile_i32(g.err) : 1;
+        sh.flag = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (sh.flag != 0) return false;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < nr; k += nw) {
+        const float2 *src = pp + ((size_t)g.parity * kMaxNR + k) * g.G;
+        FF v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int b = lane + 32 * q;
+            const float2 t = (b < g.G) ? __ldcg(src + b) : make_float2(0.f, 0.f);
+            v[q] = FF{t.x, t.y};
+        }
+        FF acc = ff_merge(ff_merge(ff_merge(v[0], v[1]), ff_merge(v[2], v[3])),
+                          ff_merge(ff_merge(v[4], v[5]), ff_merge(v[6], v[7])));
+        for (int b = lane + 256; b < g.G; b += 32) {
+            const float2 t = __ldcg(src + b);
+            acc = ff_merge(acc, FF{t.x, t.y});
+        }
+        acc = ff_shfl_tree(acc);
+        if (lane == 0) sh.out[k] = (double)acc.hi + (double)acc.lo;
+    }
+    if (threadIdx.x == 0) sh.flag2 = e;
+    g.parity ^= 1;
+    __syncthreads();
+    if (sh.flag2 != 0) return false;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) out[k] = (k < nr) ? sh.out[k] : 0.0;
+    return true;
+}
+
 struct Range {
     int s0, s1, warp, lane, nw;
 };
@@ -1614,17 +1691,18 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 const float2 vo = cur[cf.o], vv = cur[cf.v];
                 return cf.g32 * (fmaf(be, vo.y, vo.x) - fmaf(be, vv.y, vv.x));
             });
-        double blkA[1], tA[1 + kMaxCoarse];
-        block_sum_ff<1>(sh, accA, blkA);
+        double tA[1 + kMaxCoarse];
+        float2 blkA[1];
+        block_sum_ff2<1>(sh, accA, blkA);
         if (K > 0) {
-            double b9[1 + kMaxCoarse];
+            float2 b9[1 + kMaxCoarse];
             b9[0] = blkA[0];
             if (threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, rc, K, R.nw, sh.zb32);
-            for (int k = 0; k < kMaxCoarse; ++k) b9[1 + k] = (double)sh.zb32[k];
-            if (!grid_allreduce<1 + kMaxCoarse>(g, sh, b9, tA, 1 + K)) { bail(); return; }
+            for (int k = 0; k < kMaxCoarse; ++k) b9[1 + k] = make_float2(sh.zb32[k], 0.0f);
+            if (!grid_allreduce_ff<1 + kMaxCoarse>(g, sh, b9, tA, 1 + K)) { bail(); return; }
         } else {
             double o1[1];
-            if (!grid_allreduce<1>(g, sh, blkA, o1)) { bail(); return; }
+            if (!grid_allreduce_ff<1>(g, sh, blkA, o1)) { bail(); return; }
             tA[0] = o1[0];
         }
         if (threadIdx.x < 32) {
@@ -1703,9 +1781,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_mixed(SolveArgs a)
                 }
             }
         }
-        double blkB[2], tB[2];
-        block_sum_ff<2>(sh, accB, blkB);
-        if (!grid_allreduce<2>(g, sh, blkB, tB)) { bail(); return; }
+        double tB[2];
+        float2 blkB[2];
+        block_sum_ff2<2>(sh, accB, blkB);
+        if (!grid_allreduce_ff<2>(g, sh, blkB, tB)) { bail(); return; }
         ++iters;
         { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
         if (threadIdx.x == 0) {
@@ -2119,15 +2198,15 @@ __global__ void __launch_bounds__(512, 1) k_solve_fused(SolveArgs a)
             cross_sums<float>(a.cross, nx, K, sh.zbw32, [&](const CrossFace &cf) {
                 return cf.g32 * (fused_pnew(cur[cf.o], al, be, sh) - fused_pnew(cur[cf.v], al, be, sh));
             });
-        double blk[5], tP[5 + kMaxCoarse];
-        block_sum_ff<5>(sh, acc, blk);
+        double tP[5 + kMaxCoarse];
         {
-            double b[5 + kMaxCoarse];
+            float2 blk[5], b[5 + kMaxCoarse];
+            block_sum_ff2<5>(sh, acc, blk);
             for (int k = 0; k < 5; ++k) b[k] = blk[k];
             if (K > 0 && threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, rc, K, R.nw, sh.zb32);
-            for (int k = 0; k < kMaxCoarse; ++k) b[5 + k] = (K > 0) ? (double)sh.zb32[k] : 0.0;
+            for (int k = 0; k < kMaxCoarse; ++k) b[5 + k] = make_float2((K > 0) ? sh.zb32[k] : 0.0f, 0.0f);
             // also the barrier after which the next pass gathers the new state
-            if (!grid_allreduce<5 + kMaxCoarse>(g, sh, b, tP, 5 + K)) { bail(); return; }
+            if (!grid_allreduce_ff<5 + kMaxCoarse>(g, sh, b, tP, 5 + K)) { bail(); return; }
         }
         ++iters;
         { float4 *tmp = cur; cur = nxt; nxt = tmp; }
