@@ -2395,6 +2395,63 @@ __device__ __forceinline__ bool batch_allreduce(Grid &g, Shared &sh, TankState &
     return sh.flag2 == 0;
 }
 
+// The same per-tank all-reduce for double-float partials (thread 0's blk,
+// one (hi, lo) pair per value), summed per tank in double-float with FP32
+// instructions in the same order, each sum converted to FP64 at the end:
+// the batched FP32 iterations' sums, which FP64 adds would queue on GB300's
+// small FP64 pipe.
+template <int NR>
+__device__ __forceinline__ bool batch_allreduce_ff(Grid &g, Shared &sh, TankState &ts, const BatchArgs &bt,
+                                                   const float2 (&blk)[NR])
+{
+    static_assert(NR <= kBatchNR && kBatchNR <= kMaxNR, "more values than a batched all-reduce carries");
+    int e = 0;
+    __syncthreads();
+    g.epoch += 1u;
+    float2 *pp = reinterpret_cast<float2 *>(g.partials);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) pp[((size_t)g.parity * kMaxNR + k) * g.G + blockIdx.x] = blk[k];
+        const bool ok = grid_arrive_wait(g);
+        e = ok ? ld_volatile_i32(g.err) : 1;
+        sh.flag = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (sh.flag != 0) return false;
+    const int G = g.G, T = bt.T;
+    const float2 *src = pp + (size_t)g.parity * kMaxNR * G;
+    for (int i = threadIdx.x; i < NR * T; i += blockDim.x) {
+        const int k = i / T, t = i - k * T;
+        const int2 r = ts.tcta[t];
+        const int nc = r.y - r.x;
+        if (nc > kLaneSum) continue;
+        float2 v[kLaneSum];
+#pragma unroll
+        for (int q = 0; q < kLaneSum; ++q) v[q] = (q < nc) ? __ldcg(src + k * G + r.x + q) : make_float2(0.f, 0.f);
+        FF acc{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < kLaneSum; ++q)
+            if (q < nc) acc = ff_merge(acc, FF{v[q].x, v[q].y});
+        ts.tot[k][t] = (double)acc.hi + (double)acc.lo;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < NR * ts.n_wide; i += nw) {
+        const int k = i / ts.n_wide, t = ts.wide[i - k * ts.n_wide];
+        const int2 r = ts.tcta[t];
+        FF acc{0.f, 0.f};
+        for (int c = r.x + lane; c < r.y; c += 32) {
+            const float2 v = __ldcg(src + k * G + c);
+            acc = ff_merge(acc, FF{v.x, v.y});
+        }
+        acc = ff_shfl_tree(acc);
+        if (lane == 0) ts.tot[k][t] = (double)acc.hi + (double)acc.lo;
+    }
+    if (threadIdx.x == 0) sh.flag2 = e;
+    g.parity ^= 1;
+    __syncthreads();
+    return sh.flag2 == 0;
+}
+
 // Thread 0: list the tanks whose CTA count calls for a warp-wide sum.
 __device__ __forceinline__ void list_wide(TankState &ts, int T)
 {
@@ -2967,15 +3024,15 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                                         });
             }
         }
-        double blkA[1 + kTankCoarse];
+        float2 blkA[1 + kTankCoarse];
         {
-            double b1[1];
-            block_sum_ff<1>(sh, accA, b1);
+            float2 b1[1];
+            block_sum_ff2<1>(sh, accA, b1);
             blkA[0] = b1[0];
         }
         if (work && Kt > 0 && threadIdx.x < 32) finish_bins<float>(sh.zbw32, sh.zpin32, ts.rc[tank], Kt, R.nw, sh.zb32);
-        for (int k = 0; k < kTankCoarse; ++k) blkA[1 + k] = (work && k < Kt) ? (double)sh.zb32[k] : 0.0;
-        if (!batch_allreduce<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { bail(); return; }
+        for (int k = 0; k < kTankCoarse; ++k) blkA[1 + k] = make_float2((work && k < Kt) ? sh.zb32[k] : 0.0f, 0.0f);
+        if (!batch_allreduce_ff<1 + kTankCoarse>(g, sh, ts, bt, blkA)) { bail(); return; }
         if (threadIdx.x < 32) {
             zero_bins(sh);  // this pass's bins were read before the all-reduce
             for (int t = threadIdx.x; t < T; t += 32) {
@@ -3035,9 +3092,9 @@ __global__ void __launch_bounds__(512, 1) k_solve_batched(SolveArgs a, BatchArgs
                 if (i < cend) nxt[i] = cur[i];
             }
         }
-        double blkB[2];
-        block_sum_ff<2>(sh, accB, blkB);
-        if (!batch_allreduce<2>(g, sh, ts, bt, blkB)) { bail(); return; }
+        float2 blkB[2];
+        block_sum_ff2<2>(sh, accB, blkB);
+        if (!batch_allreduce_ff<2>(g, sh, ts, bt, blkB)) { bail(); return; }
         { float2 *tmp = cur; cur = nxt; nxt = tmp; }  // cur = (u_new, p)
         // Replacements come in rounds.  A tank that asks for one because its
         // FP32 residual fell a decade or 1000 iterations passed keeps
