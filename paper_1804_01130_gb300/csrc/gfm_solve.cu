@@ -2250,7 +2250,10 @@ __global__ void __launch_bounds__(512, 1) k_solve_fused(SolveArgs a)
         if (!replace_fused<CH>(a, g, sh, R, cur, sc, isc, true, restart, t, y_lane)) { bail(); return; }
         ++updates;
         if (threadIdx.x < 32) {
-            const double gam = fused_gamma(K, t[1], y_lane, sh);
+            // r.u of the state before the replacement: the recurrences' own
+            // value, which the step along the kept direction keeps using
+            const double gam_pre = fs.gam;
+            __syncwarp();
             if (threadIdx.x == 0) {
                 const double rel2 = t[0] / (fs.bnorm * fs.bnorm);
                 if (rel2 <= a.rtol * a.rtol) {
@@ -2269,16 +2272,22 @@ __global__ void __launch_bounds__(512, 1) k_solve_fused(SolveArgs a)
                     else
                         sh.ctl.action = kGo;
                 }
-                if (sh.ctl.action == kGo) {
-                    fs.gam = gam;
-                    fs.rho_max = t[3];
-                }
+                if (sh.ctl.action == kGo) fs.rho_max = t[3];
             }
             __syncwarp();
             if (sh.ctl.action == kGo) {
-                // the kept direction's p.s and t.D t are unchanged; t.D q is the new one
-                const bool ok = restart || (fs.ps > 0.0 && gam > 0.0);
-                fused_advance(K, gam, fs.ps, t[1], t[2], fs.tdt, zk_lane, y_lane, !ok, sh);
+                // Residual replacement keeps the recurrences' step: alpha from
+                // the pre-replacement r.u and the kept direction's p.s, and beta
+                // against the same r.u, while r.u of the next state is expanded
+                // from the replaced residual (its q.D q and t.D q) and the kept
+                // t.D t.  Taking alpha from the replaced residual's r.u instead
+                // let the FP32 recurrence diverge once the true residual sat at
+                // its rounding floor: that r.u is no longer the one the kept
+                // direction was built for.  After a restart (direction
+                // cleared), or when the kept direction cannot give a step, the
+                // next direction is the preconditioned residual (alpha = beta = 0).
+                const bool fresh = restart || !(fs.ps > 0.0 && gam_pre > 0.0);
+                fused_advance(K, gam_pre, fs.ps, t[1], t[2], fs.tdt, zk_lane, y_lane, fresh, sh);
             }
         }
         __syncthreads();

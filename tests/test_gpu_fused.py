@@ -104,3 +104,93 @@ def test_fused_form_rejected_on_a_batch_and_validated():
     with pytest.raises(g.GFMError):
         s.set_tuning(form=3)
     assert s.iteration_form() == 1
+
+
+def _adjoint_rhs(c, full_width=False):
+    """dL/dp: cell volumes in a band across the free surface (in 2D limited
+    in x unless full_width)."""
+    band = np.abs(c.C[1] - 0.5) < 0.15
+    if c.dims[2] == 1 and not full_width:
+        band &= (c.C[0] >= 0.5) & (c.C[0] <= 1.5)
+    return np.where(band, c.V, 0.0)
+
+
+@pytest.mark.parametrize("name", ["config1_64x32", "box_12x10x5_perm"])
+def test_fused_adjoint_matches_oracle(name):
+    """The adjoint solve (gfm_solve_adjoint) runs the same persistent solver:
+    in the fused form it meets the mixed adjoint bars of the two-pass form."""
+    c = CASES[name]()
+    w = _adjoint_rhs(c)
+    dphi_ref, dalpha_ref, mu_ref, _ = oracle.adjoint(c, w, direct=c.n <= 2048, rtol=1e-14)
+    s = _setup(c)
+    p, _, _ = s.solve(mode="fp64", rtol=1e-13)
+    dphi, dalpha, mu, info = s.adjoint(p, torch.as_tensor(w), mode="mixed", rtol=1e-12)
+    assert info.status == 0
+    assert np.max(np.abs(mu.cpu().numpy() - mu_ref)) <= 1e-7 * np.abs(mu_ref).max()
+    for got, ref in ((dphi, dphi_ref), (dalpha, dalpha_ref)):
+        assert np.max(np.abs(got.cpu().numpy() - ref)) <= 1e-5 * np.abs(ref).max()
+
+
+def test_fused_form_ends_cleanly_where_fp32_stalls():
+    """A right-hand side on which FP32 inner iterations stall near 1e-12 (the
+    full-width band on the 64x32 tank): both forms stop at a residual near the
+    request, converged or GFM_ERR_NOT_CONVERGED, and never diverge.  The fused
+    form restarts its direction on the way; a restart that kept stale step
+    data once made it blow up here."""
+    g = _g()
+    c = CASES["config1_64x32"]()
+    w = torch.as_tensor(_adjoint_rhs(c, full_width=True))
+    _, _, mu_ref, _ = oracle.adjoint(c, w.numpy(), direct=True)
+    for form in (1, 2):
+        s = _setup(c, form=form)
+        p, _, _ = s.solve(mode="fp64", rtol=1e-13)
+        _, _, mu, info = s.adjoint(p, w, mode="mixed", rtol=1e-12, raise_on_error=False)
+        assert info.status in (0, g.GFM_ERR_NOT_CONVERGED), (form, info)
+        assert info.rel_res_l2 <= 1e-11, (form, info)
+        assert np.max(np.abs(mu.cpu().numpy() - mu_ref)) <= 1e-7 * np.abs(mu_ref).max()
+
+
+def test_fused_autograd_backward():
+    g = _g()
+    c = CASES["config1_64x32"]()
+    s = g.GFM.from_case(c)
+    s.set_tuning(form=2)
+    alpha = torch.as_tensor(c.alpha).cuda().requires_grad_(True)
+    phi = torch.as_tensor(c.phi).cuda().requires_grad_(True)
+    w = torch.as_tensor(_adjoint_rhs(c)).cuda()
+    phys = dict(rho_w=c.rho_w, rho_a=c.rho_a, g=c.g, ref_cell=c.ref_cell)
+    p = g.GFMSolve.apply(alpha, phi, s, phys, dict(mode="mixed", rtol=1e-11))
+    (w * p).sum().backward()
+    dphi_ref, dalpha_ref, _, _ = oracle.adjoint(c, w.cpu().numpy(), direct=True)
+    assert np.max(np.abs(phi.grad.cpu().numpy() - dphi_ref)) <= 1e-5 * np.abs(dphi_ref).max()
+    assert np.max(np.abs(alpha.grad.cpu().numpy() - dalpha_ref)) <= 1e-5 * np.abs(dalpha_ref).max()
+
+
+def test_fused_time_step_equals_one_call_at_a_time():
+    """gfm_piso_step in the fused form: warm-started correctors, bit for bit
+    the same solves made one call at a time in the same form."""
+    c = CASES["tank_300x90"]()
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(4)
+    mesh = dict(xf=c.xf, Sf=c.Sf, spacing=(0.1, 0.1, 0.1), dims=c.dims)
+    phis = np.stack([c.phi] + [c.phi + 1e-2 ** j * cases.random_face_flux(mesh, rng, two_d=True) for j in (1, 2, 3)])
+    phys = dict(rho_w=c.rho_w, rho_a=c.rho_a, g=c.g, ref_cell=c.ref_cell, ref_value=c.ref_value)
+    s = _g().GFM.from_case(c)
+    s.set_tuning(form=2)
+    k = phis.shape[0]
+    p = torch.zeros(c.n, dtype=torch.float64, device=dev)
+    info = torch.zeros(4 * k, dtype=torch.float64, device=dev)
+    s.piso_step(torch.as_tensor(c.alpha, device=dev), torch.as_tensor(phis, device=dev), p, info,
+                V=torch.as_tensor(c.V, device=dev), rtol=1e-10, **phys)
+    torch.cuda.synchronize()
+    infos = s.infos_of_step(info, k)
+    assert all(i.status == 0 for i in infos)
+    ref = _g().GFM.from_case(c)
+    ref.set_tuning(form=2)
+    q = None
+    for j in range(k):
+        ref.assemble(torch.as_tensor(c.alpha), torch.as_tensor(phis[j]), **phys)
+        q, _, inf = ref.solve(mode="mixed", rtol=1e-10, p0=q)
+        assert inf.iters == infos[j].iters
+    assert torch.equal(p, q)
+    assert max(i.iters for i in infos[1:]) < infos[0].iters
