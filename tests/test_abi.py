@@ -81,3 +81,35 @@ def test_noalloc_wrapper_checks_sizes_before_any_device_call():
     # consistent sizes get as far as the device check: CPU tensors are refused
     with pytest.raises(gfm.GFMError, match="CUDA"):
         call()
+
+
+STRUCTS = (("gfm_mesh", "_Mesh"), ("gfm_phys", "_Phys"), ("gfm_solve_opts", "_Opts"), ("gfm_solve_info", "_Info"),
+           ("gfm_tuning", "_Tuning"), ("gfm_profile", "_Profile"))
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    of the header's structs, as a C compiler lays them out (gcc, host only)."""
+    import shutil
+    import subprocess
+    import paper_1804_01130_gb300 as gfm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gfm.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS:
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in getattr(gfm, pyname)._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, pyname in STRUCTS:
+        st = getattr(gfm, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(st), cname
+        for fname, _ in st._fields_:
+            assert got[(cname, fname)] == getattr(st, fname).offset, (cname, fname)
